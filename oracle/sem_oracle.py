@@ -1,0 +1,762 @@
+"""Plain FP64 CPU oracle for the SEM elliptic path.
+
+TEST INFRASTRUCTURE. Only the test suite, the package smoke check and the
+benchmark's CPU-baseline leg may import this module. The CUDA library never
+calls it, and it shares no code with the library: the only shared module is
+the seeded input generator ``sem_inputs`` (meshes and fields, no method
+arithmetic).
+
+Everything here is written for readability against the paper
+(Fischer et al., "NekRS, a GPU-accelerated spectral element Navier-Stokes
+solver"), Section 2 ("Spectral Element Discretization") and Section 3
+("Parallel GPU Development" / "Poisson Solve Preconditioning"), in float64:
+
+* GLL rule and derivative matrix (eq. xijk, eq. dh),
+* geometric factors (eq. grad, eq. vBu, eq. gij),
+* local operator A^e = D^T G D (+ h2 B) by sum factorisation (eq. Ae) and, for
+  tiny meshes, as explicit Kronecker-product element matrices assembled into
+  Q^T A_L Q (the "assembled stiffness matrix" below eq. dssum),
+* the gather-scatter QQ^T on global ids (the gs_op(+) interface, Section 3
+  "Parallel Communication"),
+* Jacobi-PCG, flexible PCG, Chebyshev-Jacobi smoothing and the p-multigrid
+  V-cycle with orders N, N/2 .. 1 ("Poisson Solve Preconditioning"),
+* the adjoint gradient of a mass-weighted loss with respect to nodal h1.
+
+Global (unique-node) vectors are used for every solver here; the library works
+on replicated L-vectors. Arrays of local data are shaped (E, N+1, N+1, N+1)
+with axes (e, k, j, i): point (i, j, k) of element e sits at flat index
+i + (N+1)(j + (N+1)(k + (N+1)e)), eq. uijk.
+
+Parity pins live in tests/test_oracle_*.py. Every function below is pinned
+there; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# 1-D building blocks: GLL rule, derivative and interpolation matrices
+# ----------------------------------------------------------------------------
+
+
+def legendre_pair(N: int, x):
+    """Return (P_N(x), P_{N-1}(x)) by the recurrence (k+1)P_{k+1} = (2k+1)xP_k - kP_{k-1}."""
+    x = np.asarray(x, dtype=np.float64)
+    p_prev = np.ones_like(x)
+    if N == 0:
+        return p_prev, np.zeros_like(x)
+    p = x.copy()
+    for k in range(1, N):
+        p_prev, p = p, ((2 * k + 1) * x * p - k * p_prev) / (k + 1)
+    return p, p_prev
+
+
+def gll(N: int):
+    """Gauss-Lobatto-Legendre nodes xi_0 < ... < xi_N and weights rho_j (Section 2.2).
+
+    The nodes are -1, +1 and the N-1 roots of P_N'. The roots are found by Newton's
+    method on P_N' started from the Chebyshev-Gauss-Lobatto points, with
+    P_N'(x) = N (x P_N - P_{N-1}) / (x^2 - 1) and, from Legendre's equation,
+    P_N''(x) = (2 x P_N' - N (N+1) P_N) / (1 - x^2).
+    The weights are rho_j = 2 / (N (N+1) P_N(xi_j)^2).
+    """
+    if N < 1:
+        raise ValueError("N must be >= 1")
+    xi = np.empty(N + 1)
+    xi[0], xi[N] = -1.0, 1.0
+    if N >= 2:
+        x = -np.cos(np.pi * np.arange(1, N) / N)
+        for _ in range(100):
+            P, Pm1 = legendre_pair(N, x)
+            dP = N * (x * P - Pm1) / (x * x - 1.0)
+            d2P = (2.0 * x * dP - N * (N + 1) * P) / (1.0 - x * x)
+            step = dP / d2P
+            x = x - step
+            if np.max(np.abs(step)) < 1e-16:
+                break
+        xi[1:N] = x
+    xi = 0.5 * (xi - xi[::-1])
+    P, _ = legendre_pair(N, xi)
+    rho = 2.0 / (N * (N + 1) * P * P)
+    return xi, rho
+
+
+def deriv_matrix(N: int) -> np.ndarray:
+    """D_hat[a, b] = h_b'(xi_a), eq. dh (first index: the point where the derivative is taken).
+
+    Closed form for GLL cardinal polynomials:
+    D[a, b] = P_N(xi_a) / (P_N(xi_b) (xi_a - xi_b)) for a != b,
+    D[0, 0] = -N(N+1)/4, D[N, N] = +N(N+1)/4, other diagonal entries 0.
+    """
+    xi, _ = gll(N)
+    P, _ = legendre_pair(N, xi)
+    D = np.zeros((N + 1, N + 1))
+    for a in range(N + 1):
+        for b in range(N + 1):
+            if a != b:
+                D[a, b] = P[a] / (P[b] * (xi[a] - xi[b]))
+    D[0, 0] = -N * (N + 1) / 4.0
+    D[N, N] = N * (N + 1) / 4.0
+    return D
+
+
+def lagrange_deriv_matrix(xi) -> np.ndarray:
+    """h_b'(xi_a) by differentiating the cardinal product h_b(x) = prod_{c!=b} (x-xi_c)/(xi_b-xi_c).
+
+    Independent cross-check of deriv_matrix (no Legendre closed form used).
+    """
+    xi = np.asarray(xi, dtype=np.float64)
+    n = xi.size
+    D = np.zeros((n, n))
+    for b in range(n):
+        denom = np.prod([xi[b] - xi[c] for c in range(n) if c != b])
+        for a in range(n):
+            if a == b:
+                D[a, b] = sum(1.0 / (xi[b] - xi[c]) for c in range(n) if c != b)
+            else:
+                D[a, b] = np.prod([xi[a] - xi[c] for c in range(n) if c not in (a, b)]) / denom
+    return D
+
+
+def interp_matrix(xi_from, x_to) -> np.ndarray:
+    """J[a, b] = h_b(x_a): the cardinal polynomials on nodes xi_from evaluated at points x_to."""
+    xi_from = np.asarray(xi_from, dtype=np.float64)
+    x_to = np.asarray(x_to, dtype=np.float64)
+    n = xi_from.size
+    J = np.ones((x_to.size, n))
+    for b in range(n):
+        for c in range(n):
+            if c != b:
+                J[:, b] *= (x_to - xi_from[c]) / (xi_from[b] - xi_from[c])
+    return J
+
+
+# ----------------------------------------------------------------------------
+# Tensor-product derivatives and geometry (eq. gradr-gradt, grad, vBu, gij)
+# ----------------------------------------------------------------------------
+
+
+def grad_ref(u: np.ndarray, D: np.ndarray):
+    """(u_r, u_s, u_t) = (D1 u, D2 u, D3 u) with D1 = I x I x D_hat acting on i, D2 on j, D3 on k."""
+    ur = np.einsum("ab,ekjb->ekja", D, u)
+    us = np.einsum("ab,ekbi->ekai", D, u)
+    ut = np.einsum("ab,ebji->eaji", D, u)
+    return ur, us, ut
+
+
+def grad_ref_T(wr: np.ndarray, ws: np.ndarray, wt: np.ndarray, D: np.ndarray) -> np.ndarray:
+    """D1^T wr + D2^T ws + D3^T wt (the transposed contractions of eq. Ae)."""
+    return (np.einsum("ba,ekjb->ekja", D, wr)
+            + np.einsum("ba,ekbi->ekai", D, ws)
+            + np.einsum("ba,ebji->eaji", D, wt))
+
+
+def weights3(rho: np.ndarray) -> np.ndarray:
+    """rho_ijk = rho_i rho_j rho_k laid out as [k, j, i]."""
+    return rho[:, None, None] * rho[None, :, None] * rho[None, None, :]
+
+
+def geometry(x, y, z, N: int):
+    """Geometric factors of Section 2.2.
+
+    Returns (G, B, Jac) where G has shape (6, E, NP, NP, NP) holding
+    G11, G12, G13, G22, G23, G33 of eq. gij, B = rho_ijk J_ijk (eq. vBu) and Jac
+    the Jacobian determinant. The metric matrix dx_p/dr_q = D_q x_p is inverted
+    pointwise by cofactors (eq. grad) to give dr_q/dx_p.
+    """
+    xi, rho = gll(N)
+    D = deriv_matrix(N)
+    d = [grad_ref(c, D) for c in (x, y, z)]  # d[p][q] = dx_p / dr_q
+    a, b, c = d[0]
+    dd, e, f = d[1]
+    g, h, i = d[2]
+    jac = a * (e * i - f * h) - b * (dd * i - f * g) + c * (dd * h - e * g)
+    if np.any(jac <= 0):
+        raise ValueError("non-positive Jacobian")
+    inv = [[(e * i - f * h), (c * h - b * i), (b * f - c * e)],
+           [(f * g - dd * i), (a * i - c * g), (c * dd - a * f)],
+           [(dd * h - e * g), (b * g - a * h), (a * e - b * dd)]]
+    rx = [[inv[q][p] / jac for p in range(3)] for q in range(3)]  # rx[q][p] = dr_q/dx_p
+    B = weights3(rho)[None] * jac
+    pairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    G = np.stack([(rx[m][0] * rx[n][0] + rx[m][1] * rx[n][1] + rx[m][2] * rx[n][2]) * B for m, n in pairs])
+    return G, B, jac
+
+
+def _g_full(G):
+    """3x3 symmetric view [[G11,G12,G13],[G12,G22,G23],[G13,G23,G33]]."""
+    return [[G[0], G[1], G[2]], [G[1], G[3], G[4]], [G[2], G[4], G[5]]]
+
+
+def ax_local(u, G, B, D, h1=1.0, h2=0.0):
+    """w_L = A_L u_L with A^e = D^T (h1 G) D + h2 B (eq. Ae; h2 B is the Helmholtz mass term of eq. ns_wrt2).
+
+    h1 and h2 may be scalars or arrays shaped like u (nodal coefficients).
+    """
+    ur, us, ut = grad_ref(u, D)
+    Gf = _g_full(G)
+    grads = (ur, us, ut)
+    wq = [h1 * (Gf[m][0] * grads[0] + Gf[m][1] * grads[1] + Gf[m][2] * grads[2]) for m in range(3)]
+    w = grad_ref_T(wq[0], wq[1], wq[2], D)
+    return w + h2 * B * u
+
+
+# ----------------------------------------------------------------------------
+# Global numbering, Q, Q^T and QQ^T (eq. dssum; gs_setup / gs_op semantics)
+# ----------------------------------------------------------------------------
+
+
+def gs_maps(gid) -> dict:
+    """Canonical gather-scatter maps from per-point global ids (0 = singleton).
+
+    ids   : distinct nonzero ids, ascending
+    off   : CSR offsets of each id's local points in ``idx``
+    idx   : local indices sorted by (id, local index)
+    mult  : multiplicity of each local point's node (1 for a singleton)
+    node  : unique-node number of each local point; nonzero ids take 0.. in
+            ascending id order, singletons follow in local-index order
+    label : smallest local index sharing the point's node
+    n_G   : number of unique nodes
+    """
+    g = np.asarray(gid, dtype=np.int64).ravel()
+    if np.any(g < 0):
+        raise ValueError("negative global id")
+    nL = g.size
+    loc = np.arange(nL, dtype=np.int64)
+    nz = g != 0
+    lnz, gnz = loc[nz], g[nz]
+    order = np.lexsort((lnz, gnz))
+    idx, gs = lnz[order], gnz[order]
+    start = np.ones(gs.size, dtype=bool)
+    start[1:] = gs[1:] != gs[:-1]
+    first = np.flatnonzero(start)
+    ids = gs[first]
+    off = np.append(first, gs.size).astype(np.int64)
+    m_nz = np.diff(off)
+    mult = np.ones(nL, dtype=np.int64)
+    mult[idx] = np.repeat(m_nz, m_nz)
+    node = np.empty(nL, dtype=np.int64)
+    node[idx] = np.repeat(np.arange(ids.size), m_nz)
+    zero = loc[~nz]
+    node[zero] = ids.size + np.arange(zero.size)
+    label = np.empty(nL, dtype=np.int64)
+    label[idx] = np.repeat(idx[first], m_nz)
+    label[zero] = zero
+    return {"ids": ids, "off": off, "idx": idx, "mult": mult, "node": node,
+            "label": label, "n_G": int(ids.size + zero.size)}
+
+
+def q_gather(xg, node):
+    """u_L = Q u (copy each unique value to its local points)."""
+    return xg[node]
+
+
+def q_scatter(wL, node, n_G):
+    """w = Q^T w_L (sum the local copies of each unique node)."""
+    return np.bincount(node, weights=np.ravel(wL), minlength=n_G)
+
+
+def qqt(wL, node, n_G):
+    """w_L <- QQ^T w_L (gs_op with +), eq. dssum."""
+    return q_scatter(wL, node, n_G)[node].reshape(np.shape(wL))
+
+
+# ----------------------------------------------------------------------------
+# Brute-force assembled operator for tiny meshes
+# ----------------------------------------------------------------------------
+
+
+def element_matrices(G, B, D, h1=1.0, h2=0.0):
+    """Dense A^e = sum_{m,m'} D_m^T (h1 G_mm') D_m' + h2 B from explicit Kronecker matrices (eq. Ae).
+
+    D1 = I x I x D_hat, D2 = I x D_hat x I, D3 = D_hat x I x I with the
+    i-fastest flat index i + NP j + NP^2 k.
+    """
+    NP = D.shape[0]
+    I = np.eye(NP)
+    Dm = [np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)), np.kron(D, np.kron(I, I))]
+    E = G.shape[1]
+    n = NP ** 3
+    Gf = _g_full(G)
+    h1a = np.broadcast_to(np.asarray(h1, dtype=np.float64), G.shape[1:]).reshape(E, n)
+    h2a = np.broadcast_to(np.asarray(h2, dtype=np.float64), G.shape[1:]).reshape(E, n)
+    A = np.zeros((E, n, n))
+    for e in range(E):
+        for m in range(3):
+            for mp in range(3):
+                gdiag = h1a[e] * Gf[m][mp][e].ravel()
+                A[e] += Dm[m].T @ (gdiag[:, None] * Dm[mp])
+        A[e] += np.diag(h2a[e] * B[e].ravel())
+    return A
+
+
+def assemble(Ae, node, n_G):
+    """Assembled (Neumann) matrix Q^T A_L Q as a dense array (tiny meshes only)."""
+    E, n, _ = Ae.shape
+    nd = np.asarray(node).reshape(E, n)
+    A = np.zeros((n_G, n_G))
+    for e in range(E):
+        A[np.ix_(nd[e], nd[e])] += Ae[e]
+    return A
+
+
+# ----------------------------------------------------------------------------
+# A discretisation level: geometry, numbering, Dirichlet mask, Jacobi diagonal
+# ----------------------------------------------------------------------------
+
+
+@dataclass
+class Level:
+    """One order-N discretisation of the mesh with its operator data."""
+    N: int
+    E: int
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    gid: np.ndarray
+    dirichlet: np.ndarray
+    xi: np.ndarray = field(init=False)
+    rho: np.ndarray = field(init=False)
+    D: np.ndarray = field(init=False)
+    G: np.ndarray = field(init=False)
+    B: np.ndarray = field(init=False)
+    maps: dict = field(init=False)
+
+    def __post_init__(self):
+        self.xi, self.rho = gll(self.N)
+        self.D = deriv_matrix(self.N)
+        self.G, self.B, _ = geometry(self.x, self.y, self.z, self.N)
+        self.maps = gs_maps(self.gid)
+        self.node = self.maps["node"]
+        self.n_G = self.maps["n_G"]
+        dflag = np.bincount(self.node, weights=np.ravel(self.dirichlet).astype(np.float64), minlength=self.n_G)
+        self.dir_g = dflag > 0          # Dirichlet unique nodes (rows removed by R)
+        self.free = ~self.dir_g
+
+    # -- operators on global vectors -------------------------------------------------
+    def mask(self, v):
+        """R^T R: zero the Dirichlet entries (the footnote below eq. dssum)."""
+        return np.where(self.dir_g, 0.0, v)
+
+    def apply(self, xg, h1=1.0, h2=0.0):
+        """Masked assembled operator R Q^T A_L Q R^T on a global vector."""
+        uL = q_gather(self.mask(xg), self.node).reshape(self.x.shape)
+        wL = ax_local(uL, self.G, self.B, self.D, h1, h2)
+        return self.mask(q_scatter(wL, self.node, self.n_G))
+
+    def rhs_from_nodal(self, fL):
+        """b = R Q^T B_L f_L, the GLL inner products b_i = (phi_i, f)_N (eq. qN-vBu)."""
+        return self.mask(q_scatter(self.B * fL, self.node, self.n_G))
+
+    def mass(self):
+        """Assembled diagonal mass M = Q^T B_L Q (as a global vector)."""
+        return q_scatter(self.B, self.node, self.n_G)
+
+    def diag(self, h1=1.0, h2=0.0):
+        """Exact diagonal of R Q^T A_L Q R^T (Dirichlet entries set to 1).
+
+        Per element, diag(D_m^T G D_m) at point p sums D_hat[l, p_m]^2 G_mm over
+        the line through p; the cross terms m != m' meet the diagonal only at
+        q = p and give 2 D_hat[p_m, p_m] D_hat[p_m', p_m'] G_mm'(p).
+        """
+        D = self.D
+        NP = D.shape[0]
+        Gf = _g_full(self.G)
+        h1a = np.broadcast_to(np.asarray(h1, dtype=np.float64), self.x.shape)
+        h2a = np.broadcast_to(np.asarray(h2, dtype=np.float64), self.x.shape)
+        D2 = D * D
+        d = np.einsum("li,ekjl->ekji", D2, h1a * Gf[0][0])
+        d += np.einsum("lj,ekli->ekji", D2, h1a * Gf[1][1])
+        d += np.einsum("lk,elji->ekji", D2, h1a * Gf[2][2])
+        dd = np.diag(D)
+        di = dd[None, None, None, :] * np.ones((1, NP, NP, 1))
+        dj = dd[None, None, :, None] * np.ones((1, NP, 1, NP))
+        dk = dd[None, :, None, None] * np.ones((1, 1, NP, NP))
+        d += 2.0 * h1a * (di * dj * Gf[0][1] + di * dk * Gf[0][2] + dj * dk * Gf[1][2])
+        d += h2a * self.B
+        dg = q_scatter(d, self.node, self.n_G)
+        return np.where(self.dir_g, 1.0, dg)
+
+
+def level_from_mesh(mesh: dict) -> Level:
+    return Level(mesh["N"], mesh["E"], mesh["x"], mesh["y"], mesh["z"], mesh["gid"], mesh["dirichlet"])
+
+
+# ----------------------------------------------------------------------------
+# p-multigrid level construction (orders N, N/2, ..., 1; "Poisson Solve Preconditioning")
+# ----------------------------------------------------------------------------
+
+
+def interp_local(uL, Jm):
+    """Tensor-product interpolation J x J x J applied to every element."""
+    return np.einsum("ka,jb,ic,eabc->ekji", Jm, Jm, Jm, uL)
+
+
+def interp_local_T(uL, Jm):
+    """Transpose of interp_local."""
+    return np.einsum("ak,bj,ci,eabc->ekji", Jm, Jm, Jm, uL)
+
+
+def coarse_numbering(gid_f, dir_f, Nf: int, Nc: int):
+    """Global ids and Dirichlet flags at the order-Nc points of every element.
+
+    The paper builds coarse levels of the same elements at lower order but does
+    not say how their points are numbered; this is the reading used here.
+    A coarse point is classified by how many of its indices are interior to
+    (0, Nc): none -> element vertex, one -> edge, two -> face, three -> element
+    interior (a singleton, id 0).
+    * vertex: key of the fine vertex id;
+    * edge: the edge is named by the smallest nonzero fine id on its interior,
+      the position t along it is counted from the endpoint with the smaller
+      fine id;
+    * face: the face is named by the smallest nonzero fine id on its interior;
+      the in-face position (a, b) is taken in the frame whose origin is the
+      face corner with the smallest fine id and whose first axis points to the
+      origin's neighbour corner with the smaller fine id.
+    key = (entity * 3 + type) * 256 + position, type 0/1/2 for vertex/edge/face.
+    An entity whose fine interior ids are all 0 is unshared: its points get 0.
+    The Dirichlet flag of a vertex is the fine vertex flag; of an edge or face
+    point, whether any fine point on the entity's interior is flagged.
+    """
+    E = gid_f.shape[0]
+    NPf, NPc = Nf + 1, Nc + 1
+    gf = np.asarray(gid_f, dtype=np.int64).reshape(E, NPf, NPf, NPf)
+    df = np.asarray(dir_f).reshape(E, NPf, NPf, NPf).astype(bool)
+    gc = np.zeros((E, NPc, NPc, NPc), dtype=np.int64)
+    dc = np.zeros((E, NPc, NPc, NPc), dtype=np.uint8)
+
+    def fine_at(arr, ijk):   # ijk in (i, j, k) order, each an int or a slice/array
+        i, j, k = ijk
+        return arr[:, k, j, i]
+
+    def end(c):              # coarse end index -> fine end index
+        return 0 if c == 0 else Nf
+
+    def min_nonzero(block):
+        b = block.reshape(E, -1)
+        big = np.iinfo(np.int64).max
+        m = np.where(b > 0, b, big).min(axis=1)
+        return np.where(m == big, 0, m)
+
+    for k, j, i in itertools.product(range(NPc), repeat=3):
+        c = (i, j, k)
+        mids = [d for d in range(3) if 0 < c[d] < Nc]
+        if len(mids) == 3:
+            continue
+        if len(mids) == 0:
+            fi = tuple(end(v) for v in c)
+            g = fine_at(gf, fi)
+            gc[:, k, j, i] = np.where(g > 0, (g * 3 + 0) * 256, 0)
+            dc[:, k, j, i] = fine_at(df, fi)
+        elif len(mids) == 1:
+            dd = mids[0]
+            base = [end(v) for v in c]
+            a_ijk, b_ijk = list(base), list(base)
+            a_ijk[dd], b_ijk[dd] = 0, Nf
+            gA, gB = fine_at(gf, a_ijk), fine_at(gf, b_ijk)
+            inner = list(base)
+            inner[dd] = slice(1, Nf)
+            ent = min_nonzero(fine_at(gf, inner))
+            t = np.where(gA < gB, c[dd], Nc - c[dd])
+            gc[:, k, j, i] = np.where(ent > 0, (ent * 3 + 1) * 256 + t, 0)
+            dc[:, k, j, i] = fine_at(df, inner).reshape(E, -1).any(axis=1)
+        else:
+            d1, d2 = mids
+            base = [end(v) for v in c]
+
+            def corner(s1, s2):
+                p = list(base)
+                p[d1], p[d2] = s1 * Nf, s2 * Nf
+                return fine_at(gf, p)
+
+            cg = np.stack([corner(0, 0), corner(1, 0), corner(0, 1), corner(1, 1)], 1)  # (E,4): s1 + 2 s2
+            o = np.argmin(cg, axis=1)
+            o1, o2 = o % 2, o // 2
+            n1 = cg[np.arange(E), (1 - o1) + 2 * o2]
+            n2 = cg[np.arange(E), o1 + 2 * (1 - o2)]
+            a_o = np.where(o1 == 0, c[d1], Nc - c[d1])
+            b_o = np.where(o2 == 0, c[d2], Nc - c[d2])
+            ap = np.where(n1 < n2, a_o, b_o)
+            bp = np.where(n1 < n2, b_o, a_o)
+            inner = list(base)
+            inner[d1], inner[d2] = slice(1, Nf), slice(1, Nf)
+            ent = min_nonzero(fine_at(gf, inner))
+            gc[:, k, j, i] = np.where(ent > 0, (ent * 3 + 2) * 256 + ap * 16 + bp, 0)
+            dc[:, k, j, i] = fine_at(df, inner).reshape(E, -1).any(axis=1)
+    return gc, dc
+
+
+def coarsen(fine: Level, Nc: int) -> Level:
+    """Order-Nc level on the same elements: coordinates are the fine isoparametric
+    map evaluated at the order-Nc GLL points (eq. xijk), the operator is
+    rediscretised there, and the numbering comes from coarse_numbering."""
+    xic, _ = gll(Nc)
+    Jfc = interp_matrix(fine.xi, xic)          # (NPc, NPf): fine nodal values -> coarse points
+    xc = interp_local(fine.x, Jfc)
+    yc = interp_local(fine.y, Jfc)
+    zc = interp_local(fine.z, Jfc)
+    gc, dc = coarse_numbering(fine.gid, fine.dirichlet, fine.N, Nc)
+    return Level(Nc, fine.E, xc, yc, zc, gc, dc)
+
+
+def prolong(fine: Level, coarse: Level, ec):
+    """P e_c = R_f Q_f^T W_f J_L Q_c e_c: interpolate every element, average the copies."""
+    Jcf = interp_matrix(coarse.xi, fine.xi)    # (NPf, NPc)
+    uc = q_gather(coarse.mask(ec), coarse.node).reshape(coarse.x.shape)
+    uf = interp_local(uc, Jcf)
+    w = 1.0 / fine.maps["mult"].reshape(fine.x.shape)
+    return fine.mask(q_scatter(w * uf, fine.node, fine.n_G))
+
+
+def restrict(fine: Level, coarse: Level, rf):
+    """R = P^T: r_c = R_c Q_c^T J_L^T W_f Q_f R_f^T r_f."""
+    Jcf = interp_matrix(coarse.xi, fine.xi)
+    w = 1.0 / fine.maps["mult"].reshape(fine.x.shape)
+    uf = w * q_gather(fine.mask(rf), fine.node).reshape(fine.x.shape)
+    uc = interp_local_T(uf, Jcf)
+    return coarse.mask(q_scatter(uc, coarse.node, coarse.n_G))
+
+
+def build_levels(mesh: dict, orders=None):
+    """Levels for the multigrid schedule N, N/2, ..., 1 (default) or the given orders."""
+    top = level_from_mesh(mesh)
+    if orders is None:
+        orders = [top.N]
+        while orders[-1] > 1:
+            orders.append(max(1, orders[-1] // 2))
+    if orders[0] != top.N:
+        raise ValueError("first order must be the mesh order")
+    levels = [top]
+    for Nc in orders[1:]:
+        levels.append(coarsen(levels[-1], Nc))
+    return levels
+
+
+# ----------------------------------------------------------------------------
+# Krylov solvers, smoother, eigenvalue estimate, V-cycle
+# ----------------------------------------------------------------------------
+
+
+def splitmix64(seed: int, counters) -> np.ndarray:
+    """SplitMix64 (Steele, Lea & Flood 2014), counter form mix(seed + (c+1)*0x9E3779B97F4A7C15)."""
+    c = np.asarray(counters).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (c + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def lanczos_start(level: Level, seed: int = 1):
+    """Seeded start vector: U[-1,1) per unique node, drawn at the node's smallest local index."""
+    label = level.maps["label"]
+    first = np.zeros(level.n_G, dtype=np.int64)
+    first[level.node] = label
+    u = (splitmix64(seed, first) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return level.mask(2.0 * u - 1.0)
+
+
+def lanczos_lmax(apply, dinv, v0, steps: int = 10) -> float:
+    """Largest Ritz value of ``steps`` Lanczos steps on S = D^{-1/2} A D^{-1/2} (same spectrum as D^{-1} A)."""
+    s = np.sqrt(dinv)
+    v = v0 / np.linalg.norm(v0)
+    v_prev = np.zeros_like(v)
+    beta = 0.0
+    alphas, betas = [], []
+    for j in range(steps):
+        w = s * apply(s * v) - beta * v_prev
+        alpha = float(w @ v)
+        w = w - alpha * v
+        alphas.append(alpha)
+        beta = float(np.linalg.norm(w))
+        if j == steps - 1 or beta == 0.0:
+            break
+        betas.append(beta)
+        v_prev, v = v, w / beta
+    T = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
+    return float(np.linalg.eigvalsh(T).max())
+
+
+def cheb_smooth(apply, dinv, b, x, lmin: float, lmax: float, degree: int):
+    """Chebyshev-accelerated Jacobi, ``degree`` steps on A x = b (Saad, Alg. 12.1 form).
+
+    theta = (lmax+lmin)/2, delta = (lmax-lmin)/2, sigma = theta/delta, rho = 1/sigma;
+    d = D^{-1} r / theta, x += d; then for each further step:
+    r = b - A x, rho' = 1/(2 sigma - rho), d = rho' rho d + (2 rho'/delta) D^{-1} r, x += d.
+    ``x`` None means a zero initial guess (r = b without a matvec).
+    """
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    if x is None:
+        r = b
+        x = np.zeros_like(b)
+    else:
+        r = b - apply(x)
+    d = dinv * r / theta
+    x = x + d
+    for _ in range(1, degree):
+        r = b - apply(x)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * (dinv * r)
+        x = x + d
+        rho = rho_new
+    return x
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    iters: int
+    relres: float
+    history: list
+
+
+def pcg(apply, b, minv, tol: float, maxit: int, flexible: bool = False) -> SolveResult:
+    """Preconditioned CG from x0 = 0 (Saad, Alg. 9.1), stopping when ||r||/||b|| <= tol.
+
+    With ``flexible`` the Polak-Ribiere form beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k)
+    is used (flexible CG, "Poisson Solve Preconditioning"); otherwise
+    beta = (z_{k+1}, r_{k+1}) / (z_k, r_k).
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = float(np.linalg.norm(b))
+    hist = [1.0]
+    if bnorm == 0.0:
+        return SolveResult(x, 0, 0.0, hist)
+    z = minv(r)
+    p = z.copy()
+    rz = float(r @ z)
+    k = 0
+    relres = 1.0
+    while k < maxit:
+        w = apply(p)
+        alpha = rz / float(p @ w)
+        x = x + alpha * p
+        r_old = r
+        r = r - alpha * w
+        k += 1
+        relres = float(np.linalg.norm(r)) / bnorm
+        hist.append(relres)
+        if relres <= tol:
+            break
+        z = minv(r)
+        if flexible:
+            beta = float(z @ (r - r_old)) / rz
+        else:
+            beta = float(z @ r) / rz
+        rz = float(r @ z)
+        p = z + beta * p
+    return SolveResult(x, k, relres, hist)
+
+
+@dataclass
+class MGParams:
+    degree: int = 2
+    lmin_factor: float = 0.1
+    lmax_factor: float = 1.1
+    lanczos_steps: int = 10
+    lanczos_seed: int = 1
+    coarse_tol: float = 1e-4
+    coarse_maxit: int = 100
+    lmax: list | None = None     # per smoothed level; estimated by Lanczos when None
+
+
+class PMG:
+    """p-multigrid V-cycle with Chebyshev-Jacobi smoothing on every level but the
+    coarsest and a Jacobi-PCG coarse solve ("Poisson Solve Preconditioning")."""
+
+    def __init__(self, levels, h1=1.0, h2=0.0, params: MGParams | None = None):
+        self.levels = levels
+        self.h1, self.h2 = h1, h2
+        self.p = params or MGParams()
+        self.dinv = [np.where(L.free, 1.0 / L.diag(h1, h2), 0.0) for L in levels]
+        self.ops = [(lambda v, L=L: L.apply(v, h1, h2)) for L in levels]
+        if self.p.lmax is None:
+            self.lmax = [lanczos_lmax(self.ops[l], self.dinv[l], lanczos_start(levels[l], self.p.lanczos_seed),
+                                      self.p.lanczos_steps) for l in range(len(levels) - 1)]
+        else:
+            self.lmax = list(self.p.lmax)
+        self.coarse_iters = []
+
+    def smooth(self, l, b, x):
+        lam = self.lmax[l]
+        return cheb_smooth(self.ops[l], self.dinv[l], b, x, self.p.lmin_factor * lam,
+                           self.p.lmax_factor * lam, self.p.degree)
+
+    def vcycle(self, l, r):
+        if l == len(self.levels) - 1:
+            res = pcg(self.ops[l], r, lambda v: self.dinv[l] * v, self.p.coarse_tol, self.p.coarse_maxit)
+            self.coarse_iters.append(res.iters)
+            return res.x
+        x = self.smooth(l, r, None)
+        res = r - self.ops[l](x)
+        ec = self.vcycle(l + 1, restrict(self.levels[l], self.levels[l + 1], res))
+        x = x + prolong(self.levels[l], self.levels[l + 1], ec)
+        return self.smooth(l, r, x)
+
+    def __call__(self, r):
+        return self.vcycle(0, r)
+
+
+def solve(level: Level, b, h1=1.0, h2=0.0, tol=1e-8, maxit=1000, precond="jacobi",
+          levels=None, params: MGParams | None = None) -> SolveResult:
+    """Solve R Q^T A_L Q R^T x = b: Jacobi-PCG, or flexible PCG with the p-MG V-cycle."""
+    op = lambda v: level.apply(v, h1, h2)
+    if precond == "jacobi":
+        dinv = np.where(level.free, 1.0 / level.diag(h1, h2), 0.0)
+        return pcg(op, b, lambda v: dinv * v, tol, maxit)
+    if precond == "pmg":
+        mg = PMG(levels, h1, h2, params)
+        res = pcg(op, b, mg, tol, maxit, flexible=True)
+        res.mg = mg
+        return res
+    raise ValueError(precond)
+
+
+# ----------------------------------------------------------------------------
+# Adjoint gradient with respect to nodal h1
+# ----------------------------------------------------------------------------
+
+
+def grad_h1_local(level: Level, uL, lamL):
+    """g_L = -sum_{m,m'} (D_m lam) G_mm' (D_m' u) at every local point (G without h1).
+
+    For A(h1) = Q^T [D^T (h1 G) D] Q with h1 nodal, dA/dh1 at a local point is the
+    pointwise factor of eq. Ae, so dL/dh1 = -lam^T (dA/dh1) u with A lam = dL/du.
+    """
+    lr, ls, lt = grad_ref(lamL, level.D)
+    ur, us, ut = grad_ref(uL, level.D)
+    Gf = _g_full(level.G)
+    gl = (lr, ls, lt)
+    gu = (ur, us, ut)
+    acc = np.zeros_like(uL)
+    for m in range(3):
+        for mp in range(3):
+            acc += gl[m] * Gf[m][mp] * gu[mp]
+    return -acc
+
+
+def adjoint_loss_and_grads(level: Level, fL, h1L, h2, u_target_L, tol=1e-13, maxit=5000):
+    """Loss L = 1/2 sum_l B_l (u_l - t_l)^2 over local points, u_L = Q u with A(h1, h2) u = R Q^T B_L f_L.
+
+    For continuous u_L and t_L this is 1/2 (u - t)^T M (u - t) with the assembled
+    mass M = Q^T B_L Q. Returns (L, u, lam, dL/df_L, dL/dh1_L): the adjoint solve
+    A lam = R Q^T (dL/du_L) uses the symmetry of A (A = R Q^T A_L Q R^T is SPD),
+    dL/df_L = B_L Q lam and dL/dh1_L is grad_h1_local.
+    """
+    b = level.rhs_from_nodal(fL)
+    u = solve(level, b, h1L, h2, tol=tol, maxit=maxit).x
+    uL = q_gather(u, level.node).reshape(level.x.shape)
+    gL = level.B * (uL - u_target_L)
+    loss = 0.5 * float(np.sum(level.B * (uL - u_target_L) ** 2))
+    lam = solve(level, level.mask(q_scatter(gL, level.node, level.n_G)), h1L, h2, tol=tol, maxit=maxit).x
+    lamL = q_gather(lam, level.node).reshape(level.x.shape)
+    dfL = level.B * lamL
+    dh1L = grad_h1_local(level, uL, lamL)
+    return loss, u, lam, dfL, dh1L
