@@ -1,0 +1,334 @@
+"""Benchmark: FP64 matrix-free Ax + gather-scatter throughput (GDOF/s) on the
+warped 32^3-element N=7 box, plus the p-multigrid PCG time to a 1e-8 relative
+residual on the 24^3-element N=7 pressure problem.
+
+A step is one assembled operator application w_L = R QQ^T A_L u_L (sem_ax with
+SEM_AX_ASSEMBLE: the Ax kernel then the gather-scatter+mask kernel) on inputs
+resident in HBM. value = unique DOFs (n_G) per second over the timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank runs an independent replica on its own GPU
+(the path has no exchange step on one box): value sums the ranks' DOFs over
+the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GDOF/s of Ax+gather-scatter and PCG time-to-1e-8 at N=7, vs HBM roofline"
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4          # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz over 152 SMs
+SM_MAX_MHZ = 2070.0
+
+
+def ax_flops_per_element(N: int, helmholtz: bool = True) -> int:
+    """The paper's count for A^e u^e, 12(N+1)^4 + 15(N+1)^3, plus 2(N+1)^3 for h2 B u."""
+    NP = N + 1
+    return 12 * NP ** 4 + 15 * NP ** 3 + (2 * NP ** 3 if helmholtz else 0)
+
+
+def ax_gs_bytes(nL: int, n_shared: int, nG: int, helmholtz: bool = True) -> int:
+    """Algorithmic bytes of one FP64 Ax+gs: 6 G (+B) per local point, a 4-byte id per
+    non-interior local point, u read and w written once per unique node."""
+    return (56 if helmholtz else 48) * nL + 4 * n_shared + 16 * nG
+
+
+def peaks():
+    p = {"hbm_gbs": 6686.5, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        p = {"hbm_gbs": d.get("hbm_gbs", 6686.5), "source": "measured"}
+    p["fp64_tflops"] = SM_COUNT * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------------
+def oracle_ax_gs_rate(mesh, budget_s: float = 12.0):
+    """Time the oracle's FP64 local Ax on a growing sample of elements (bounded CPU time)
+    and scale to GDOF/s through the unique-DOF share of a local point."""
+    import oracle as O
+
+    N, E = mesh["N"], mesh["E"]
+    nL = mesh["x"].size
+    nG = int(mesh["gid"].max())
+    D = O.deriv_matrix(N)
+    u = mesh["u"]
+    k = 64
+    spent, pts, calls = 0.0, 0, 0
+    while spent < budget_s and k <= E:
+        sl = slice(0, k)
+        G, B, _ = O.geometry(mesh["x"][sl], mesh["y"][sl], mesh["z"][sl], N)
+        t0 = time.perf_counter()
+        w = O.ax_local(u[sl], G, B, D, 1.0, 0.5)
+        O.qqt(w, O.gs_maps(mesh["gid"][sl])["node"], int(w.size))
+        dt = time.perf_counter() - t0
+        spent += dt
+        pts += w.size
+        calls += 1
+        k = min(E, k * 2) if k < E else E + 1
+    rate_local = pts / spent
+    return {"value": rate_local * nG / nL / 1e9, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle ax_local+qqt (numpy, FP64) on the first 64..{k // 2} elements of the "
+                      f"{E}-element box, {calls} calls, {pts} local points in {spent:.1f} s; "
+                      f"scaled by n_G/n_L = {nG / nL:.4f}"}
+
+
+# ----------------------------------------------------------------------------------
+def build_mesh(e1: int, N: int):
+    import sem_inputs as si
+
+    mesh = si.box_mesh(e1, N, warp=0.1, perm_seed=0)
+    mesh["u"] = si.uniform_field(mesh, 0)
+    return mesh
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    mesh = build_mesh(args.elements, 7)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(oracle_ax_gs_rate(mesh, budget_s=max(2.0, 20.0 / (args.warmup + args.steps))))
+    timed = vals[args.warmup:]
+    v = statistics.median([t["value"] for t in timed])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Ax+gs, FP64 Helmholtz (h1=1, h2=0.5), {args.elements}^3 warped box, N=7"},
+            "cpu_baseline": {**timed[-1], "value": v},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_events(fn, steps, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def solve_bench(ctx_cls, args, dev):
+    """PCG time to ||r||/||b|| <= 1e-8 on the 24^3-element N=7 warped pressure problem."""
+    import torch
+
+    import sem_inputs as si
+
+    mesh = si.box_mesh(args.solve_elements, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
+    ctx = ctx_cls.from_mesh(mesh)
+    b = torch.tensor(si.gaussian_assembled_rhs(mesh, 0).ravel(), device=dev)
+    out = {"workload": f"{args.solve_elements}^3 warped box, N=7, x=0 Dirichlet, Gaussian zero-mean RHS, "
+                       f"FCG + p-MG (7-3-1, Chebyshev-Jacobi degree 2, coarse Jacobi-PCG) to 1e-8",
+           "n_L": int(mesh["x"].size), "n_G": int(ctx.levels[0]["nG"])}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "fp32", "bf16g"):
+        ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled")   # warm-up incl. setup
+        times, info = [], None
+        for _ in range(args.solve_reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled")
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        t = min(times)
+        out[prec] = {"time_to_1e-8_s": t, "median_s": statistics.median(times), "iters": info["iters"],
+                     "ms_per_iter": 1e3 * t / max(1, info["iters"]), "relres": info["relres"],
+                     "coarse_iters": info["coarse_iters"]}
+    if args.jacobi:
+        ctx.solve(b, tol=1e-8, maxit=20000, precond="jacobi", rhs="assembled")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = ctx.solve(b, tol=1e-8, maxit=20000, precond="jacobi", rhs="assembled")
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out["jacobi_fp64"] = {"time_to_1e-8_s": t, "iters": info["iters"], "ms_per_iter": 1e3 * t / info["iters"],
+                              "relres": info["relres"]}
+    ctx.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--elements", type=int, default=32, help="elements per side of the Ax box")
+    ap.add_argument("--solve-elements", type=int, default=24)
+    ap.add_argument("--solve-reps", type=int, default=3)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--jacobi", action="store_true", help="also time Jacobi-PCG on the solve problem")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2104_05829_gb300 import SemContext
+
+    mesh = build_mesh(args.elements, 7)
+    ctx = SemContext.from_mesh(mesh, prec_copies=0, mg_orders=[7])
+    lv = ctx.levels[0]
+    nL, nG, n_shared, E = lv["nL"], lv["nG"], lv["n_seg_idx"], lv["E"]
+    u = torch.tensor(mesh["u"].ravel(), device=dev)
+    w = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+
+    step = lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t = time_events(step, args.steps, stream)
+        # dominant kernel alone: the local Ax launch, same stream, same inputs
+        t_ax = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False), args.steps, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    ms = 1e3 * t / args.steps
+    value = world * nG * args.steps / t / 1e9
+
+    pk = peaks()
+    flops = ax_flops_per_element(7) * E
+    t_ax_launch = t_ax / args.steps
+    achieved_tf = flops / t_ax_launch / 1e12
+    bytes_alg = ax_gs_bytes(nL, n_shared, nG)
+    roof = {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": achieved_tf / pk["fp64_tflops"], "traffic": None,
+            "kernel": "k_ax<double,double,8> (FP64 local Ax)",
+            "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+            "hbm_view": {"bytes_per_step": bytes_alg, "achieved_gbs": bytes_alg / (ms / 1e3) / 1e9,
+                         "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                         "peak_source": pk["source"]}}
+
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FP64 Helmholtz Ax+gs (h1=1, h2=0.5) on a {args.elements}^3-element warped "
+                                   f"unit-cube box, N=7, u ~ U[-1,1] continuous (seed 0)",
+                       "E": E, "N": 7, "n_L": nL, "n_G": nG, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (1.1 GB read per step vs 129 MB L2)"},
+            "roofline": roof, "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary()}
+
+    if not args.no_e2e:
+        # end to end through the public API: pinned host u -> device, Ax+gs, w -> pinned host
+        uh = torch.tensor(mesh["u"].ravel()).pin_memory()
+        wh = torch.empty_like(uh).pin_memory()
+
+        def e2e_step():
+            u.copy_(uh, non_blocking=True)
+            ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True)
+            wh.copy_(w, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = time_events(e2e_step, args.steps, stream)
+        line["e2e"] = {"value": world * nG * args.steps / te / 1e9, "unit": "GDOF/s",
+                       "h2d_bytes_per_step": 8 * nL, "d2h_bytes_per_step": 8 * nL, "ms_per_step": 1e3 * te / args.steps}
+    ctx.close()
+    if not args.no_solve:
+        line["solve"] = solve_bench(SemContext, args, dev)
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = oracle_ax_gs_rate(mesh)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * sem.h - C ABI of libsem: the matrix-free spectral-element elliptic solver
+ * path of NekRS (Fischer et al., "NekRS, a GPU-accelerated spectral element
+ * Navier-Stokes solver"), written for one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Section 2.2, eq. aip/A and the Helmholtz substep eq. ns_wrt2):
+ *   find u with  A u = b,  A = R Q^T A_L Q R^T,
+ *   A^e = D^T (h1 G^e) D + h2 B^e            (eq. Ae, eq. gij, eq. vBu)
+ * on E hexahedral elements of order N with GLL points. Q is the Boolean
+ * global-to-local map built from per-point global ids (eq. dssum and the
+ * gs_setup interface of Section 3, "Parallel Communication"); R removes
+ * Dirichlet rows (footnote below eq. dssum).
+ *
+ * Vectors. Every vector passed to the library is an L-vector: E blocks of
+ * (N+1)^3 values, point (i,j,k) of element e at index
+ * i + (N+1)*(j + (N+1)*(k + (N+1)*e)) (eq. uijk). A "continuous" L-vector
+ * holds the same value in every local copy of a global node. Solver inputs
+ * and outputs are continuous L-vectors.
+ *
+ * Memory and streams. Unless stated otherwise vector arguments are DEVICE
+ * pointers owned by the caller (e.g. torch tensors), contiguous, 8-byte (FP64)
+ * or 4-byte (FP32) aligned; the library keeps no reference to them after the
+ * call returns. Mesh arrays in sem_setup are HOST pointers, copied. All
+ * internal device memory (geometric factors, gather-scatter maps, multigrid
+ * levels, solver workspace) is allocated in sem_setup and released by
+ * sem_free; sem_ax, sem_gs and the level operators allocate nothing.
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ * calls are asynchronous on it except where noted.
+ *
+ * Errors. Every int-returning call returns SEM_OK (0) or a negative code
+ * below; sem_strerror gives a message and sem_last_error_detail the last
+ * failure's context. No call exits, aborts or traps.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_OK 0
+#define SEM_EINVAL (-1)      /* bad argument: N, E, id, pointer, level, flag */
+#define SEM_ENOMEM (-2)      /* device allocation failed */
+#define SEM_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define SEM_ENOTCONV (-4)    /* maxit reached before the tolerance; info is filled */
+#define SEM_EBREAKDOWN (-5)  /* Krylov breakdown: p^T A p <= 0 or a NaN/Inf scalar */
+#define SEM_EMESH (-6)       /* mesh rejected: non-positive Jacobian in some element */
+
+#define SEM_MAX_N 11         /* orders 1..SEM_MAX_N are compiled */
+#define SEM_MAX_LEVELS 6
+
+/* Arithmetic of an operator application. */
+#define SEM_FP64 0           /* FP64 geometric factors and arithmetic */
+#define SEM_FP32 1           /* FP32 geometric factors and arithmetic */
+#define SEM_BF16G 2          /* BF16 geometric factors, FP32 arithmetic */
+
+/* sem_ax / sem_level_ax flags */
+#define SEM_AX_LOCAL 0       /* w_L = A_L u_L only (no assembly) */
+#define SEM_AX_ASSEMBLE 1    /* w_L = R QQ^T A_L u_L (gs_op(+) then Dirichlet mask) */
+
+/* sem_gs flags */
+#define SEM_GS_ADD 0         /* w_L <- QQ^T w_L */
+#define SEM_GS_ADD_MASK 1    /* w_L <- R QQ^T w_L (zero every copy of a Dirichlet node) */
+
+/* sem_solve preconditioners and flags */
+#define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */
+#define SEM_PC_PMG 1         /* flexible PCG + p-multigrid V-cycle with Chebyshev-Jacobi smoothing */
+#define SEM_RHS_NODAL 0      /* f_L is a nodal function: b = R Q^T B_L f_L, replicated */
+#define SEM_RHS_ASSEMBLED 1  /* f_L already holds the assembled b, replicated on copies */
+#define SEM_X0_GIVEN 2       /* use u_L on entry as the initial guess (else x0 = 0) */
+
+/* precision bits in sem_opts.prec_copies: which preconditioner copies to build */
+#define SEM_BUILD_FP32 1
+#define SEM_BUILD_BF16G 2
+
+typedef struct sem_ctx sem_ctx;
+
+/* Mesh description (all HOST pointers, copied during sem_setup). */
+typedef struct {
+  int32_t E;                 /* number of elements, >= 1 */
+  int32_t N;                 /* polynomial order, 1..SEM_MAX_N */
+  const double* x;           /* E*(N+1)^3 nodal coordinates at the GLL points (eq. xijk) */
+  const double* y;
+  const double* z;
+  const int64_t* gid;        /* E*(N+1)^3 global node ids, >= 0; 0 marks a singleton (gs_setup) */
+  const uint8_t* dirichlet;  /* E*(N+1)^3 flags, 1 = Dirichlet point; NULL = pure Neumann */
+} sem_mesh;
+
+/* Solver/multigrid options. sem_default_opts fills the defaults given here. */
+typedef struct {
+  int32_t mg_nlevels;        /* 0: schedule N, N/2, ..., 1; else the number of orders in mg_orders */
+  int32_t mg_orders[SEM_MAX_LEVELS]; /* strictly decreasing, mg_orders[0] == N */
+  int32_t cheb_degree;       /* Chebyshev-Jacobi steps per smoothing application (2) */
+  double cheb_lmin_factor;   /* smoothed interval [lmin*est, lmax*est] (0.1) */
+  double cheb_lmax_factor;   /* (1.1) */
+  int32_t lanczos_steps;     /* Lanczos steps for the eigenvalue estimate of D^-1 A (10) */
+  uint64_t lanczos_seed;     /* SplitMix64 seed of the Lanczos start vector (1) */
+  double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-4) */
+  int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
+  int32_t prec_copies;       /* SEM_BUILD_* bits: FP32 / BF16 factor copies (SEM_BUILD_FP32|SEM_BUILD_BF16G) */
+} sem_opts;
+
+/* Coefficients h1 (diffusion) and h2 (mass) of A = D^T h1 G D + h2 B. */
+typedef struct {
+  double h1;
+  double h2;
+  const double* h1_L;        /* DEVICE, optional nodal h1 on the fine level (L-vector); NULL = scalar h1 */
+} sem_coef;
+
+/* Per-solve report. */
+typedef struct {
+  int32_t iters;             /* outer Krylov iterations */
+  double relres;             /* final ||r|| / ||b|| (unique-node 2-norm) */
+  double bnorm;              /* ||b|| */
+  int32_t coarse_iters;      /* total coarse-level PCG iterations (PMG only) */
+  int32_t nlevels;
+  double lmax[SEM_MAX_LEVELS]; /* Lanczos estimates of lambda_max(D^-1 A) per smoothed level */
+} sem_info;
+
+/* Per-level sizes. */
+typedef struct {
+  int32_t N, E;
+  int64_t nL;                /* E*(N+1)^3 local points */
+  int64_t nG;                /* unique global nodes */
+  int64_t n_ids;             /* distinct nonzero global ids */
+  int64_t n_idx;             /* local points with a nonzero id */
+  int64_t n_seg;             /* gather-scatter segments (shared or Dirichlet nodes) */
+  int64_t n_seg_idx;         /* local points in those segments */
+} sem_level_desc;
+
+void sem_default_opts(sem_opts* opts);
+const char* sem_strerror(int code);
+const char* sem_last_error_detail(void);
+
+/* Build everything the path needs on the current CUDA device (Section 2.2 and
+ * "Parallel Communication"): GLL rule and D_hat (eq. dh) per order, geometric
+ * factors G and B in FP64 (eq. grad, eq. gij, eq. vBu) plus FP32/BF16 copies,
+ * the canonical gather-scatter maps (gs_setup), the Dirichlet mask and the
+ * multigrid levels. Synchronous. Errors: SEM_EINVAL (bad N/E/pointer, negative
+ * id), SEM_EMESH (J <= 0 somewhere), SEM_ENOMEM, SEM_ECUDA. On error *out is NULL. */
+int sem_setup(const sem_mesh* mesh, const sem_opts* opts, sem_ctx** out);
+void sem_free(sem_ctx* ctx);
+
+int sem_num_levels(const sem_ctx* ctx);
+int sem_level_info(const sem_ctx* ctx, int level, sem_level_desc* out);
+
+/* w_L = A_L u_L (flags SEM_AX_LOCAL) or R QQ^T A_L u_L (SEM_AX_ASSEMBLE) on the
+ * fine level in FP64, A^e = D^T h1 G D + h2 B (eq. Ae). u_L and w_L must not
+ * alias. Errors: SEM_EINVAL, SEM_ECUDA. */
+int sem_ax(sem_ctx* ctx, const double* u_L, double* w_L, const sem_coef* coef, int flags, void* stream);
+
+/* w_L <- QQ^T w_L (SEM_GS_ADD) or R QQ^T w_L (SEM_GS_ADD_MASK) on the fine
+ * level in FP64: the gs_op(+) of "Parallel Communication". In place. */
+int sem_gs(sem_ctx* ctx, double* w_L, int flags, void* stream);
+
+/* Level operators (level 0 = fine, 1.. coarser). `prec` selects SEM_FP64
+ * (double vectors) or SEM_FP32/SEM_BF16G (float vectors; the copy must have
+ * been built). h1/h2 are scalars here. */
+int sem_level_ax(sem_ctx* ctx, int level, int prec, const void* u_L, void* w_L, double h1, double h2,
+                 int flags, void* stream);
+int sem_level_gs(sem_ctx* ctx, int level, int prec, void* w_L, int flags, void* stream);
+
+/* Inverse of the exact assembled diagonal of A on `level` (Jacobi, Section
+ * 2.2), replicated on copies, 0 at Dirichlet nodes. FP64 output. */
+int sem_level_dinv(sem_ctx* ctx, int level, double h1, double h2, double* dinv_L, void* stream);
+
+/* Multigrid transfers between level `level` (fine) and `level`+1 (coarse)
+ * ("Poisson Solve Preconditioning", orders N, N/2, ..., 1):
+ *   prolong : x_f += R_f J e_c  (J: tensor interpolation, e_c continuous)
+ *   restrict: r_c  = R_c QQ^T_c J^T (W_f r_f), W_f the counting weight 1/m. */
+int sem_prolong_add(sem_ctx* ctx, int level, int prec, const void* ec_L, void* xf_L, void* stream);
+int sem_restrict(sem_ctx* ctx, int level, int prec, const void* rf_L, void* rc_L, void* stream);
+
+/* Set up the preconditioner for coefficients (h1, h2): Jacobi diagonals and
+ * Lanczos estimates of lambda_max(D^-1 A) on every smoothed level, in the
+ * arithmetic `prec` of the V-cycle. Synchronous. */
+int sem_precond_setup(sem_ctx* ctx, double h1, double h2, int prec, void* stream);
+/* Chebyshev-Jacobi smoothing on `level` (needs sem_precond_setup): x <- S(b, x);
+ * x_is_zero != 0 treats x as 0 on entry. Vectors in the V-cycle's precision. */
+int sem_cheb_smooth(sem_ctx* ctx, int level, const void* b_L, void* x_L, int x_is_zero, void* stream);
+/* z_L = M r_L: one V-cycle (needs sem_precond_setup), FP64 in and out. */
+int sem_vcycle(sem_ctx* ctx, const double* r_L, double* z_L, void* stream);
+/* Read back the lambda_max estimates (after sem_precond_setup). */
+int sem_get_lmax(const sem_ctx* ctx, double* lmax, int n);
+
+/* Solve A u = b to ||r||/||b|| <= tol with Jacobi-PCG (SEM_PC_JACOBI) or
+ * flexible PCG preconditioned by the p-MG V-cycle (SEM_PC_PMG) whose
+ * smoother and levels run in `prec` (SEM_FP64, SEM_FP32, SEM_BF16G); the
+ * outer iteration, residual and dot products are always FP64. f_L: nodal
+ * function or assembled b (rhs_flags). u_L: solution (continuous L-vector).
+ * Blocks until done (reads one residual norm per iteration). Errors:
+ * SEM_ENOTCONV (info filled, u_L holds the last iterate), SEM_EBREAKDOWN,
+ * SEM_EINVAL, SEM_ECUDA. info may be NULL. */
+int sem_solve(sem_ctx* ctx, const double* f_L, const sem_coef* coef, double tol, int maxit, int precond,
+              int prec, int rhs_flags, double* u_L, sem_info* info, void* stream);
+
+/* Adjoint gradient with respect to nodal h1 (no counterpart in the paper's
+ * solver; built on eq. Ae): g_L = -sum_{m,m'} (D_m lam)(G_mm')(D_m' u) at every
+ * local point, with G excluding h1. For L = loss(u(h1)), A lam = dL/du gives
+ * dL/dh1 = g. flags 0: per-point contributions (the gradient with respect to
+ * an L-vector h1); SEM_GRAD_SUM: summed over the copies of each node (QQ^T),
+ * the gradient with respect to the unique nodal values, replicated. */
+#define SEM_GRAD_SUM 1
+int sem_grad_h1(sem_ctx* ctx, const double* u_L, const double* lam_L, double* g_L, int flags, void* stream);
+
+/* b_L = R QQ^T (B_L f_L): the GLL inner products b_i = (phi_i, f)_N (eq. qN-vBu). */
+int sem_rhs(sem_ctx* ctx, const double* f_L, double* b_L, void* stream);
+/* out_L = B_L f_L, the local diagonal mass (eq. vBu), no assembly. */
+int sem_mass_local(sem_ctx* ctx, const double* f_L, double* out_L, void* stream);
+
+/* Unique-node dot product (a, b) of two continuous FP64 L-vectors: the sum
+ * over one owner copy of each non-Dirichlet node. Result in *out (HOST). Synchronous. */
+int sem_dot(sem_ctx* ctx, const double* a_L, const double* b_L, double* out, void* stream);
+
+/* ---- read-back of setup products, for validation (HOST outputs, synchronous) ---- */
+/* Canonical gather-scatter maps of `level` (any pointer may be NULL):
+ * ids[n_ids]: distinct nonzero global ids ascending; off[n_ids+1]: CSR offsets;
+ * idx[n_idx]: local indices sorted by (id, local index); mult[nL]: multiplicity;
+ * node[nL]: unique-node number (ids in order, then singletons in local order);
+ * label[nL]: smallest local index of the point's node; dmask[nL]: 1 at Dirichlet nodes. */
+int sem_get_maps(const sem_ctx* ctx, int level, int64_t* ids, int64_t* off, int32_t* idx, int32_t* mult,
+                 int64_t* node, int64_t* label, uint8_t* dmask);
+/* FP64 geometric factors [E][7][(N+1)^3] (G11,G12,G13,G22,G23,G33,B) of `level`. */
+int sem_get_geom(const sem_ctx* ctx, int level, double* G);
+/* BF16 / FP32 copies as raw bits (uint16 / uint32 per value, same layout). */
+int sem_get_geom_lowp(const sem_ctx* ctx, int level, int prec, void* G);
+/* Nodal coordinates and global ids of `level` (coarse levels are derived). */
+int sem_get_coords(const sem_ctx* ctx, int level, double* x, double* y, double* z, int64_t* gid);
+/* GLL nodes, weights and D_hat (row-major, D[a*(N+1)+b] = h_b'(xi_a)) for order N. */
+int sem_gll(int N, double* xi, double* rho, double* D);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H */

@@ -1,0 +1,10 @@
+"""GB300-native spectral-element elliptic solver path (NekRS, Section 2.2 / 3).
+
+The compute lives in libsem.so (CUDA, sm_103a); this package holds its build
+script and a thin Python binding. Nothing here falls back to the CPU: if the
+library is not built, every call raises.
+"""
+from ._lib import SemError, load  # noqa: F401
+from .sem import SemContext, default_opts, gll  # noqa: F401
+
+__all__ = ["SemContext", "SemError", "default_opts", "gll", "load"]

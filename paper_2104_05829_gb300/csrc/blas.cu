@@ -1,0 +1,465 @@
+// Vector kernels of the Krylov solvers and the Chebyshev smoother.
+//
+// Dot products are unique-node inner products of continuous L-vectors: the sum
+// over one owner copy of every non-Dirichlet node (equal to the counting-
+// weighted sum of the paper's w-weighted reductions, but with one product per
+// node). Reductions are deterministic: a fixed grid of RED_BLOCKS blocks walks
+// the vector with a fixed stride, each block reduces in a fixed shuffle tree,
+// and the last block to finish (atomic ticket) adds the block partials in
+// index order and finalises the Krylov scalars on the device. Nothing spins.
+//
+// Scalars (alpha, beta, residual norms) live in a device array `sc` so that a
+// whole iteration runs without the host; sc[S_DONE] != 0 turns every kernel
+// of that loop into a no-op (device-side convergence).
+#include "sem_internal.cuh"
+
+namespace sem {
+
+namespace {
+
+template <int NS>
+struct Sums {
+  double v[NS];
+};
+
+template <int NS>
+__device__ __forceinline__ void warp_sum(Sums<NS>& a) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a.v[s] += __shfl_xor_sync(0xffffffffu, a.v[s], o);
+}
+
+// Block-reduce `a`, publish the block partial, and let the last block combine
+// all partials in index order and call fin(totals).
+template <int NS, class Fin>
+__device__ void reduce_finish(Sums<NS> a, double* part, unsigned* ticket, Fin fin) {
+  __shared__ double s_w[RED_THREADS / 32][NS];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum(a);
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = a.v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
+      part[s * gridDim.x + blockIdx.x] = t;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  Sums<NS> b;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double t = 0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(part + s * gridDim.x + q);
+    b.v[s] = t;
+  }
+  warp_sum(b);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = b.v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sums<NS> tot;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
+      tot.v[s] = t;
+    }
+    fin(tot);
+    *ticket = 0u;
+  }
+}
+
+__device__ __forceinline__ bool skip(const double* sc) { return sc && sc[S_DONE] != 0.0; }
+
+#define GRID_LOOP(l, n) \
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (n); l += (int64_t)gridDim.x * blockDim.x)
+
+// ---- plain dot ---------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_dot(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const uint8_t* __restrict__ own,
+          double* part, unsigned* ticket, double* out) {
+  Sums<1> acc{{0}};
+  GRID_LOOP(l, n) {
+    if (own[l]) acc.v[0] = fma((double)a[l], (double)b[l], acc.v[0]);
+  }
+  reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) { *out = t.v[0]; });
+}
+
+// ---- PCG start: r = b (- w), x = 0 unless given, p = dinv r; (b,b), (r, dinv r) ----
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_pcg_begin(int64_t n, const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ x, T* __restrict__ r,
+                const T* __restrict__ dinv, T* __restrict__ p, const uint8_t* __restrict__ own, double* part,
+                unsigned* ticket, double* sc, double tol) {
+  Sums<3> acc{{0, 0, 0}};
+  GRID_LOOP(l, n) {
+    const T bl = b[l];
+    T rl = bl;
+    if (w) rl = bl - w[l];
+    else x[l] = T(0);
+    r[l] = rl;
+    const T zl = dinv ? dinv[l] * rl : rl;
+    if (p) p[l] = zl;
+    if (own[l]) {
+      acc.v[0] = fma((double)bl, (double)bl, acc.v[0]);
+      acc.v[1] = fma((double)rl, (double)zl, acc.v[1]);
+      acc.v[2] = fma((double)rl, (double)rl, acc.v[2]);
+    }
+  }
+  reduce_finish<3>(acc, part, ticket, [=] __device__(const Sums<3>& t) {
+    sc[S_BB] = t.v[0];
+    sc[S_RZ] = t.v[1];
+    sc[S_RR] = t.v[2];
+    sc[S_TOL2] = tol * tol * t.v[0];
+    sc[S_ITER] = 0;
+    sc[S_BREAK] = 0;
+    sc[S_DONE] = (t.v[2] <= tol * tol * t.v[0]) ? 1.0 : 0.0;
+  });
+}
+
+// ---- alpha = (r,z)/(p,w) ---------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_alpha(int64_t n, const T* __restrict__ p, const T* __restrict__ w, const uint8_t* __restrict__ own,
+            double* part, unsigned* ticket, double* sc) {
+  if (skip(sc)) return;
+  Sums<1> acc{{0}};
+  GRID_LOOP(l, n) {
+    if (own[l]) acc.v[0] = fma((double)p[l], (double)w[l], acc.v[0]);
+  }
+  reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) {
+    const double pw = t.v[0];
+    sc[S_PW] = pw;
+    if (!(pw > 0.0) || !isfinite(pw)) {
+      sc[S_BREAK] = 1;
+      sc[S_DONE] = 1;
+      sc[S_ALPHA] = 0;
+    } else {
+      sc[S_ALPHA] = sc[S_RZ] / pw;
+    }
+  });
+}
+
+// ---- Jacobi-PCG update: x += a p, r -= a w; (r,r), (r, dinv r); beta ------------
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+    k_update_jacobi(int64_t n, T* __restrict__ x, const T* __restrict__ p, T* __restrict__ r,
+                    const T* __restrict__ w, const T* __restrict__ dinv, const uint8_t* __restrict__ own,
+                    double* part, unsigned* ticket, double* sc) {
+  if (skip(sc)) return;
+  const T a = (T)sc[S_ALPHA];
+  Sums<2> acc{{0, 0}};
+  GRID_LOOP(l, n) {
+    x[l] = fma(a, p[l], x[l]);
+    const T rl = fma(-a, w[l], r[l]);
+    r[l] = rl;
+    if (own[l]) {
+      const double rd = (double)rl;
+      acc.v[0] = fma(rd, rd, acc.v[0]);
+      acc.v[1] = fma(rd, (double)(dinv[l] * rl), acc.v[1]);
+    }
+  }
+  reduce_finish<2>(acc, part, ticket, [=] __device__(const Sums<2>& t) {
+    sc[S_RR] = t.v[0];
+    sc[S_ITER] += 1;
+    sc[S_TOTAL] += 1;
+    sc[S_BETA] = t.v[1] / sc[S_RZ];
+    sc[S_RZ] = t.v[1];
+    if (!isfinite(t.v[0])) {
+      sc[S_BREAK] = 1;
+      sc[S_DONE] = 1;
+    }
+    if (t.v[0] <= sc[S_TOL2]) sc[S_DONE] = 1;
+  });
+}
+
+template <typename T>
+__global__ void k_direction_jacobi(int64_t n, T* __restrict__ p, const T* __restrict__ r,
+                                   const T* __restrict__ dinv, const double* sc) {
+  if (skip(sc)) return;
+  const T beta = (T)sc[S_BETA];
+  GRID_LOOP(l, n) p[l] = fma(beta, p[l], dinv[l] * r[l]);
+}
+
+// ---- flexible CG (FP64) ----------------------------------------------------------
+__global__ void __launch_bounds__(RED_THREADS)
+    k_update_flex(int64_t n, double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
+                  const double* __restrict__ w, double* __restrict__ dr, const uint8_t* __restrict__ own,
+                  double* part, unsigned* ticket, double* sc) {
+  if (skip(sc)) return;
+  const double a = sc[S_ALPHA];
+  Sums<1> acc{{0}};
+  GRID_LOOP(l, n) {
+    x[l] = fma(a, p[l], x[l]);
+    const double ro = r[l];
+    const double rn = fma(-a, w[l], ro);
+    r[l] = rn;
+    dr[l] = rn - ro;
+    if (own[l]) acc.v[0] = fma(rn, rn, acc.v[0]);
+  }
+  reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) {
+    sc[S_RR] = t.v[0];
+    sc[S_ITER] += 1;
+    if (!isfinite(t.v[0])) {
+      sc[S_BREAK] = 1;
+      sc[S_DONE] = 1;
+    }
+    if (t.v[0] <= sc[S_TOL2]) sc[S_DONE] = 1;
+  });
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_beta_flex(int64_t n, const double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ dr,
+                const uint8_t* __restrict__ own, double* part, unsigned* ticket, double* sc) {
+  if (skip(sc)) return;
+  Sums<2> acc{{0, 0}};
+  GRID_LOOP(l, n) {
+    if (own[l]) {
+      const double zl = z[l];
+      acc.v[0] = fma(zl, r[l], acc.v[0]);
+      acc.v[1] = fma(zl, dr[l], acc.v[1]);
+    }
+  }
+  reduce_finish<2>(acc, part, ticket, [=] __device__(const Sums<2>& t) {
+    sc[S_BETA] = t.v[1] / sc[S_RZ];
+    sc[S_RZ] = t.v[0];
+    sc[S_ZDR] = t.v[1];
+    if (!isfinite(t.v[0]) || !isfinite(t.v[1])) {
+      sc[S_BREAK] = 1;
+      sc[S_DONE] = 1;
+    }
+  });
+}
+
+__global__ void k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* sc) {
+  if (skip(sc)) return;
+  const double beta = sc[S_BETA];
+  GRID_LOOP(l, n) p[l] = fma(beta, p[l], z[l]);
+}
+
+// ---- Chebyshev-Jacobi pieces (no reductions) -------------------------------------
+// first step: d = inv_theta * dinv * (b - w) (w null: x was 0, r = b); x = x + d
+template <typename T>
+__global__ void k_cheb_first(int64_t n, const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ x,
+                             T* __restrict__ d, const T* __restrict__ dinv, T inv_theta, int x_zero) {
+  GRID_LOOP(l, n) {
+    const T r = w ? b[l] - w[l] : b[l];
+    const T dl = inv_theta * (dinv[l] * r);
+    d[l] = dl;
+    x[l] = x_zero ? dl : x[l] + dl;
+  }
+}
+
+// later steps: d = c1 d + c2 dinv (b - w); x += d
+template <typename T>
+__global__ void k_cheb_step(int64_t n, const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ x,
+                            T* __restrict__ d, const T* __restrict__ dinv, T c1, T c2) {
+  GRID_LOOP(l, n) {
+    const T r = b[l] - w[l];
+    const T dl = c1 * d[l] + c2 * (dinv[l] * r);
+    d[l] = dl;
+    x[l] += dl;
+  }
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+  GRID_LOOP(l, n) b[l] = (B)a[l];
+}
+
+template <typename T>
+__global__ void k_fill(int64_t n, T* __restrict__ v, T val) {
+  GRID_LOOP(l, n) v[l] = val;
+}
+
+__global__ void k_dinv(int64_t n, double* __restrict__ d, const uint8_t* __restrict__ dmask, float* __restrict__ d32) {
+  GRID_LOOP(l, n) {
+    const double v = dmask[l] ? 0.0 : 1.0 / d[l];
+    d[l] = v;
+    if (d32) d32[l] = (float)v;
+  }
+}
+
+__global__ void k_rhs_mass(int64_t n, int np3, const double* __restrict__ f, const double* __restrict__ G,
+                           double* __restrict__ b) {
+  GRID_LOOP(l, n) {
+    const int64_t e = l / np3;
+    const int loc = (int)(l - e * np3);
+    b[l] = G[(e * 7 + 6) * np3 + loc] * f[l];
+  }
+}
+
+template <typename T>
+__global__ void k_mul_cwt(int64_t n, const T* __restrict__ a, const T* __restrict__ c, T* __restrict__ o) {
+  GRID_LOOP(l, n) o[l] = c[l] * a[l];
+}
+
+inline unsigned vgrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+int vec_fill(void* v, int prec, int64_t n, double val, cudaStream_t s) {
+  if (prec == SEM_FP64) k_fill<double><<<vgrid(n), 256, 0, s>>>(n, (double*)v, val);
+  else k_fill<float><<<vgrid(n), 256, 0, s>>>(n, (float*)v, (float)val);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int vec_copy_convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaStream_t s) {
+  const bool s64 = sprec == SEM_FP64, d64 = dprec == SEM_FP64;
+  if (s64 && d64) SEM_CUDA_TRY(cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, s));
+  else if (!s64 && !d64) SEM_CUDA_TRY(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, s));
+  else if (s64) k_convert<double, float><<<vgrid(n), 256, 0, s>>>(n, (const double*)src, (float*)dst);
+  else k_convert<float, double><<<vgrid(n), 256, 0, s>>>(n, (const float*)src, (double*)dst);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int dot_owner(Ctx& C, const Level& L, int prec, const void* a, const void* b, double* d_out, cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_dot<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const double*)a, (const double*)b, L.owner,
+                                                     C.red_part, C.red_ticket, d_out);
+  else
+    k_dot<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const float*)a, (const float*)b, L.owner, C.red_part,
+                                                    C.red_ticket, d_out);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int dinv_finalize(const Level& L, double* d, float* d32, cudaStream_t s) {
+  k_dinv<<<vgrid(L.nL), 256, 0, s>>>(L.nL, d, L.dmask, d32);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int dinv_finalize(const Level& L, double* d, cudaStream_t s) { return dinv_finalize(L, d, nullptr, s); }
+
+int rhs_mass(const Level& L, const double* f, double* b, cudaStream_t s) {
+  k_rhs_mass<<<vgrid(L.nL), 256, 0, s>>>(L.nL, L.NP * L.NP * L.NP, f, L.G, b);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int mul_counting_weight(const Level& L, int prec, const void* in, void* out, cudaStream_t s) {
+  if (prec == SEM_FP64) k_mul_cwt<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const double*)in, L.cwt, (double*)out);
+  else k_mul_cwt<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const float*)in, L.cwt32, (float*)out);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int pcg_begin_tol(Ctx& C, const Level& L, int prec, const void* b, const void* w, void* x, void* r,
+                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_pcg_begin<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
+                                                           (double*)r, (const double*)dinv, (double*)p, L.owner,
+                                                           C.red_part, C.red_ticket, sc, tol);
+  else
+    k_pcg_begin<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x,
+                                                          (float*)r, (const float*)dinv, (float*)p, L.owner,
+                                                          C.red_part, C.red_ticket, sc, tol);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_alpha(Ctx& C, const Level& L, int prec, const void* p, const void* w, double* sc, cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_alpha<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const double*)p, (const double*)w, L.owner,
+                                                       C.red_part, C.red_ticket, sc);
+  else
+    k_alpha<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const float*)p, (const float*)w, L.owner, C.red_part,
+                                                      C.red_ticket, sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_update_jacobi(Ctx& C, const Level& L, int prec, void* x, const void* p, void* r, const void* w,
+                     const void* dinv, double* sc, cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_update_jacobi<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (double*)x, (const double*)p, (double*)r,
+                                                               (const double*)w, (const double*)dinv, L.owner,
+                                                               C.red_part, C.red_ticket, sc);
+  else
+    k_update_jacobi<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (float*)x, (const float*)p, (float*)r,
+                                                              (const float*)w, (const float*)dinv, L.owner,
+                                                              C.red_part, C.red_ticket, sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_direction_jacobi(const Level& L, int prec, void* p, const void* r, const void* dinv, double* sc,
+                        cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_direction_jacobi<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (double*)p, (const double*)r,
+                                                           (const double*)dinv, sc);
+  else
+    k_direction_jacobi<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (float*)p, (const float*)r, (const float*)dinv,
+                                                          sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, double* dr,
+                   double* sc, cudaStream_t s) {
+  k_update_flex<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, x, p, r, w, dr, L.owner, C.red_part, C.red_ticket, sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_beta_flex(Ctx& C, const Level& L, const double* z, const double* r, const double* dr, double* sc,
+                 cudaStream_t s) {
+  k_beta_flex<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, z, r, dr, L.owner, C.red_part, C.red_ticket, sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int kr_direction(const Level& L, double* p, const double* z, double* sc, cudaStream_t s) {
+  k_direction<<<vgrid(L.nL), 256, 0, s>>>(L.nL, p, z, sc);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, void* d, bool x_zero,
+               double inv_theta, cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_cheb_first<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
+                                                     (double*)d, L.dinv, inv_theta, x_zero ? 1 : 0);
+  else
+    k_cheb_first<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
+                                                    L.dinv32, (float)inv_theta, x_zero ? 1 : 0);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, void* d, double c1, double c2,
+              cudaStream_t s) {
+  if (prec == SEM_FP64)
+    k_cheb_step<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
+                                                    (double*)d, L.dinv, c1, c2);
+  else
+    k_cheb_step<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
+                                                   L.dinv32, (float)c1, (float)c2);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+}  // namespace sem

@@ -1,0 +1,196 @@
+// Internal declarations shared by the libsem translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "sem.h"
+
+namespace sem {
+
+// ----------------------------------------------------------------------------
+// Error plumbing: every entry point returns a status; the last failure's text
+// is kept per host thread for sem_last_error_detail.
+// ----------------------------------------------------------------------------
+void set_detail(const char* fmt, ...);
+
+#define SEM_CUDA_TRY(call)                                                             \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::sem::set_detail("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return SEM_ECUDA;                                                                \
+    }                                                                                  \
+  } while (0)
+
+#define SEM_LAUNCH_CHECK() SEM_CUDA_TRY(cudaGetLastError())
+
+#define SEM_TRY(expr)          \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != SEM_OK) return rc_; \
+  } while (0)
+
+// Small dense matrices passed to kernels by value (they land in the kernel's
+// constant parameter bank; kernels copy them to shared memory where the index
+// depends on the thread).
+struct Mat64 {
+  double a[144];
+};
+struct Mat32 {
+  float a[144];
+};
+
+inline int np3(int N) { return (N + 1) * (N + 1) * (N + 1); }
+
+// Host-side 1-D rule for order N (GLL nodes ascending, weights, D_hat row-major
+// D[a*(N+1)+b] = h_b'(xi_a), eq. dh).
+void host_gll(int N, double* xi, double* rho);
+void host_dhat(int N, const double* xi, double* D);
+// J[a*nc + b] = h_b(x_a) for cardinal polynomials on xi_from (nc nodes) at points x_to.
+void host_interp(int nc, const double* xi_from, int nt, const double* x_to, double* J);
+
+struct Level {
+  int N = 0, NP = 0, E = 0;
+  int64_t nL = 0, nG = 0, n_ids = 0, n_idx = 0, n_seg = 0, n_seg_idx = 0;
+  Mat64 D{};                 // D_hat of this order
+  Mat32 Df{};
+  double xi[16] = {0}, rho[16] = {0};
+  // geometry: [E][7][NP^3] with components G11 G12 G13 G22 G23 G33 B
+  double* G = nullptr;
+  float* G32 = nullptr;
+  __nv_bfloat16* G16 = nullptr;
+  // coordinates, ids and Dirichlet flags as given (fine) or derived (coarse)
+  double *x = nullptr, *y = nullptr, *z = nullptr;
+  int64_t* gid = nullptr;
+  uint8_t* dflag = nullptr;
+  // canonical gather-scatter maps
+  int64_t* ids = nullptr;    // [n_ids]
+  int64_t* off = nullptr;    // [n_ids+1]
+  int32_t* idx = nullptr;    // [n_idx]
+  int32_t* mult = nullptr;   // [nL]
+  int32_t* node = nullptr;   // [nL]
+  int32_t* label = nullptr;  // [nL]
+  uint8_t* dmask = nullptr;  // [nL] 1 at Dirichlet nodes
+  uint8_t* owner = nullptr;  // [nL] 1 at the smallest-index copy of each non-Dirichlet node
+  double* cwt = nullptr;     // [nL] counting weight 1/m
+  float* cwt32 = nullptr;
+  // gather-scatter segments: nodes that are shared or Dirichlet
+  int32_t* seg_off = nullptr;  // [n_seg+1]
+  int32_t* seg_idx = nullptr;  // [n_seg_idx]
+  uint8_t* seg_dir = nullptr;  // [n_seg]
+  // interpolation from level+1 (coarse) to this level: J[a*NPc + b] = h^c_b(xi^f_a)
+  Mat64 Jc{};
+  Mat32 Jcf{};
+  // preconditioner state
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  double lmax = 0.0;
+  // V-cycle work vectors (allocated in the precision of the build: FP64 and FP32 sets)
+  double *vb = nullptr, *vx = nullptr, *vr = nullptr, *vd = nullptr, *vw = nullptr;
+  float *fb = nullptr, *fx = nullptr, *fr = nullptr, *fd = nullptr, *fw = nullptr;
+  double *cp = nullptr;      // extra FP64 vector (coarse PCG direction)
+  float *cpf = nullptr;
+};
+
+// Device scalar slots (double) used by the Krylov kernels.
+enum Scal {
+  S_RZ = 0,      // (r, z)
+  S_PW,          // (p, w)
+  S_ALPHA,
+  S_RR,          // (r, r)
+  S_RZN,         // (r, z) new
+  S_ZDR,         // (z, r_new - r_old)
+  S_BETA,
+  S_BB,          // (b, b)
+  S_DONE,        // nonzero: the loop has converged; kernels become no-ops
+  S_BREAK,       // nonzero: breakdown seen
+  S_TOL2,        // tol^2 * (b,b) for device-side convergence tests
+  S_ITER,        // iterations counted on the device
+  S_TOTAL,       // iterations summed over every loop started since the last reset
+  S_NSLOTS
+};
+
+struct Ctx {
+  int device = 0;
+  int nlevels = 0;
+  Level lev[SEM_MAX_LEVELS];
+  sem_opts opts{};
+  // deterministic reduction scratch
+  double* red_part = nullptr;       // [RED_BLOCKS * 4]
+  unsigned int* red_ticket = nullptr;
+  double* scal = nullptr;           // [4 * S_NSLOTS]: outer, coarse, spare
+  double* h_scal = nullptr;         // pinned mirror
+  // fine-level FP64 solver workspace
+  double *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *dr = nullptr, *t = nullptr;
+  // preconditioner
+  bool pc_ready = false;
+  int pc_prec = SEM_FP64;
+  double pc_h1 = 0, pc_h2 = 0;
+  cudaEvent_t ev = nullptr;
+};
+
+constexpr int RED_BLOCKS = 304;   // 2 per SM on a 152-SM GB300; fixed for determinism
+constexpr int RED_THREADS = 256;
+
+// ---- ax.cu
+int ax_apply(const Level& L, int prec, const void* u, void* w, double h1, double h2, const double* h1L,
+             cudaStream_t s, const double* skip = nullptr);
+int diag_local(const Level& L, double h1, double h2, const double* h1L, double* d, cudaStream_t s);
+int grad_h1_apply(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
+int geom_compute(Level& L, int* d_bad, cudaStream_t s);
+
+// ---- gs.cu
+int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);
+int gs_apply_skip(const Level& L, int prec, void* w, bool mask, const double* skip, cudaStream_t s);
+
+// ---- gsmap.cu
+int build_maps(Level& L, cudaStream_t s);
+
+// ---- blas.cu
+int vec_fill(void* v, int prec, int64_t n, double val, cudaStream_t s);
+int vec_copy_convert(const void* src, int sprec, void* dst, int dprec, int64_t n, cudaStream_t s);
+int dot_owner(Ctx& C, const Level& L, int prec, const void* a, const void* b, double* d_out, cudaStream_t s);
+int dinv_finalize(const Level& L, double* d, cudaStream_t s);
+int dinv_finalize(const Level& L, double* d, float* d32, cudaStream_t s);
+int rhs_mass(const Level& L, const double* f, double* b, cudaStream_t s);
+int mul_counting_weight(const Level& L, int prec, const void* in, void* out, cudaStream_t s);
+
+// Krylov / smoother kernels (blas.cu)
+int pcg_begin_tol(Ctx& C, const Level& L, int prec, const void* b, const void* w, void* x, void* r,
+                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s);
+int kr_alpha(Ctx& C, const Level& L, int prec, const void* p, const void* w, double* sc, cudaStream_t s);
+int kr_update_jacobi(Ctx& C, const Level& L, int prec, void* x, const void* p, void* r, const void* w,
+                     const void* dinv, double* sc, cudaStream_t s);
+int kr_direction_jacobi(const Level& L, int prec, void* p, const void* r, const void* dinv, double* sc,
+                        cudaStream_t s);
+int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, double* dr,
+                   double* sc, cudaStream_t s);
+int kr_beta_flex(Ctx& C, const Level& L, const double* z, const double* r, const double* dr, double* sc,
+                 cudaStream_t s);
+int kr_direction(const Level& L, double* p, const double* z, double* sc, cudaStream_t s);
+int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, void* d, bool x_zero,
+               double inv_theta, cudaStream_t s);
+int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, void* d, double c1, double c2,
+              cudaStream_t s);
+int residual_weighted(const Level& L, int prec, const void* b, const void* w, void* out, cudaStream_t s);
+
+// ---- solve.cu
+int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s);
+int vcycle(Ctx& C, int prec, const double* r, double* z, cudaStream_t s);
+
+// ---- transfer (ax.cu)
+int interp_add(const Level& F, const Level& Cl, int prec, const void* ec, void* xf, cudaStream_t s);
+int interp_T(const Level& F, const Level& Cl, int prec, const void* rf, void* rc, cudaStream_t s);
+// rc = J^T (cwt_f * (bf - wf)) without assembly (wf may be null)
+int restrict_residual(const Level& F, const Level& Cl, int prec, const void* bf, const void* wf, void* rc,
+                      cudaStream_t s);
+
+// helpers
+inline size_t prec_size(int prec) { return prec == SEM_FP64 ? 8 : 4; }
+
+}  // namespace sem

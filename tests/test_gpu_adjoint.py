@@ -1,0 +1,86 @@
+"""Adjoint gradient kernel and the differentiable solve vs the oracle and
+central finite differences (the loss is 1/2 sum_l B_l (u_l - t_l)^2)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import sem_inputs as si
+from gpu_common import H, T, ctx_for, dev, relmax
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("N", [2, 5, 7, 11])
+def test_grad_h1_kernel(N):
+    dev()
+    mesh = si.box_mesh((3, 2, 2), N, warp=0.1, perm_seed=N)
+    ctx = ctx_for(mesh, prec_copies=0)
+    lev = O.level_from_mesh(mesh)
+    rng = np.random.default_rng(N)
+    u = rng.standard_normal(mesh["x"].shape)
+    lam = rng.standard_normal(mesh["x"].shape)
+    g = H(ctx.grad_h1(T(u), T(lam)))
+    ref = O.grad_h1_local(lev, u, lam).ravel()
+    assert relmax(g, ref) < 1e-12
+    gs = H(ctx.grad_h1(T(u), T(lam), sum_copies=True))
+    assert relmax(gs, O.qqt(ref, lev.node, lev.n_G)) < 1e-12
+
+
+def _problem(e=4, N=7):
+    mesh = si.box_mesh(e, N, warp=0.1, perm_seed=0)
+    h1 = np.exp(0.5 * si.smooth_random_field(mesh, 1))
+    t = si.smooth_random_field(mesh, 2)
+    f = si.smooth_random_field(mesh, 3)
+    return mesh, h1, t, f
+
+
+def test_autograd_matches_oracle_adjoint():
+    dev()
+    from paper_2104_05829_gb300.autograd import helmholtz_solve
+    mesh, h1, t, f = _problem(e=2, N=5)
+    ctx = ctx_for(mesh, prec_copies=0)
+    lev = O.level_from_mesh(mesh)
+    ft = T(f).requires_grad_(True)
+    ht = T(h1).requires_grad_(True)
+    tt = T(t)
+    B = ctx.mass_local(torch.ones_like(tt))
+    u = helmholtz_solve(ctx, ft, ht, h2=1.0, tol=1e-13)
+    loss = 0.5 * torch.sum(B * (u - tt) ** 2)
+    loss.backward()
+    lo, uo, lam, dfo, dho = O.adjoint_loss_and_grads(lev, f, h1, 1.0, t)
+    assert abs(loss.item() - lo) < 1e-10 * abs(lo)
+    assert relmax(H(ft.grad), dfo.ravel()) < 1e-8
+    assert relmax(H(ht.grad), dho.ravel()) < 1e-8
+
+
+def test_autograd_finite_differences_4x4x4_N7():
+    """Central differences of GPU solves along a continuous direction, E = 4^3, N = 7."""
+    dev()
+    from paper_2104_05829_gb300.autograd import helmholtz_solve
+    mesh, h1, t, f = _problem(e=4, N=7)
+    ctx = ctx_for(mesh, prec_copies=0)
+    lev = O.level_from_mesh(mesh)
+    tt = T(t)
+    B = ctx.mass_local(torch.ones_like(tt))
+
+    def loss_of(fv, hv):
+        u = helmholtz_solve(ctx, fv, hv, h2=1.0, tol=1e-13)
+        return 0.5 * torch.sum(B * (u - tt) ** 2)
+
+    ft = T(f).requires_grad_(True)
+    ht = T(h1).requires_grad_(True)
+    loss_of(ft, ht).backward()
+    rng = np.random.default_rng(0)
+    v = T(O.q_gather(rng.standard_normal(lev.n_G), lev.node))
+    with torch.no_grad():
+        for grad, which in ((ht.grad, "h1"), (ft.grad, "f")):
+            dd = torch.dot(grad, v).item()
+            fd = []
+            for eps in (1e-3, 1e-4):
+                def at(s):
+                    return (loss_of(T(f), T(h1) + s * v) if which == "h1" else loss_of(T(f) + s * v, T(h1))).item()
+                fd.append((at(eps) - at(-eps)) / (2 * eps))
+            assert abs(fd[-1] - dd) < 1e-6 * abs(dd), (which, fd, dd)
+            if which == "h1":
+                assert abs(fd[0] - dd) > 10 * abs(fd[1] - dd)

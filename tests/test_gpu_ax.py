@@ -1,0 +1,128 @@
+"""GPU operator kernels vs the oracle through the C ABI.
+
+Tolerances (norm-wise, max|gpu - oracle| / max|oracle|):
+* FP64 Ax and gather-scatter: 1e-12 (the paper's FP64 operator; the two
+  sides differ only in summation order, a few ulp times the ~N terms per sum);
+* FP32 Ax: 2e-6 (unit roundoff 6e-8 times the O(N) terms and the factor
+  rounding);
+* FP32 arithmetic with BF16 factors: 2e-2 (BF16 keeps 8 bits: 2^-9 = 2e-3 per
+  factor, amplified by cancellation in the contraction sums).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import sem_inputs as si
+from gpu_common import H, T, ctx_for, dev, global_from_L, relmax
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _setup(shape, N, warp=0.1, seed=0, **kw):
+    mesh = si.box_mesh(shape, N, warp=warp, perm_seed=seed, **kw)
+    return mesh, ctx_for(mesh), O.level_from_mesh(mesh)
+
+
+@pytest.mark.parametrize("N", range(1, 12))
+def test_ax_local_fp64_all_orders(N):
+    dev()
+    mesh, ctx, lev = _setup((3, 2, 5), N, seed=N)   # 30 elements: ragged for every block size
+    rng = np.random.default_rng(N)
+    u = rng.uniform(-1, 1, mesh["x"].shape)
+    for h1, h2 in ((1.0, 0.0), (0.8, 0.5)):
+        w = H(ctx.ax(T(u), h1=h1, h2=h2, assemble=False))
+        ref = O.ax_local(u, lev.G, lev.B, lev.D, h1, h2).ravel()
+        assert relmax(w, ref) < 1e-12, (N, h1, h2)
+
+
+def test_ax_local_fp64_nodal_h1():
+    dev()
+    mesh, ctx, lev = _setup((4, 3, 2), 7)
+    g = si.smooth_random_field(mesh, seed=1)
+    h1 = np.exp(0.5 * g)
+    u = si.uniform_field(mesh, 0)
+    w = H(ctx.ax(T(u), h1_L=T(h1), h2=1.0, assemble=False))
+    assert relmax(w, O.ax_local(u, lev.G, lev.B, lev.D, h1, 1.0).ravel()) < 1e-12
+
+
+@pytest.mark.parametrize("N,dirichlet", [(7, si.FACES), (3, ("x0",)), (5, ())])
+def test_ax_assembled_fp64(N, dirichlet):
+    dev()
+    mesh, ctx, lev = _setup((4, 4, 3), N, dirichlet=dirichlet)
+    u = si.uniform_field(mesh, 0)          # continuous field
+    w = H(ctx.ax(T(u), h1=1.0, h2=0.5, assemble=True))
+    ug = global_from_L(lev, u)
+    ref = O.q_gather(lev.apply(ug, 1.0, 0.5), lev.node)
+    assert relmax(w, ref) < 1e-12
+
+
+def test_gs_matches_oracle_qqt():
+    dev()
+    mesh, ctx, lev = _setup((5, 3, 4), 4, dirichlet=("y0", "z1"))
+    v = np.random.default_rng(0).standard_normal(mesh["x"].size)
+    got = H(ctx.gs(T(v)))
+    ref = O.qqt(v, lev.node, lev.n_G)
+    assert relmax(got, ref) < 1e-15
+    got = H(ctx.gs(T(v), mask=True))
+    refm = np.where(lev.dir_g[lev.node], 0.0, ref)
+    assert relmax(got, refm) < 1e-15
+    ones = H(ctx.gs(T(np.ones(mesh["x"].size))))
+    np.testing.assert_array_equal(ones, lev.maps["mult"])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("bf16g", 2e-2)])
+def test_ax_low_precision(prec, tol):
+    dev()
+    mesh, ctx, lev = _setup((4, 3, 3), 7)
+    u = si.uniform_field(mesh, 0)
+    w = H(ctx.level_ax(0, T(u, torch.float32), h1=1.0, h2=0.5, prec=prec, assemble=False))
+    ref = O.ax_local(u, lev.G, lev.B, lev.D, 1.0, 0.5).ravel()
+    assert relmax(w, ref) < tol
+
+
+def test_level_ax_on_coarse_levels():
+    dev()
+    mesh = si.box_mesh((3, 3, 2), 7, warp=0.1, perm_seed=1, dirichlet=("x0",))
+    ctx = ctx_for(mesh)
+    levels = O.build_levels(mesh, [7, 3, 1])
+    for l in (1, 2):
+        Lo = levels[l]
+        u = np.random.default_rng(l).standard_normal(Lo.x.size)
+        w = H(ctx.level_ax(l, T(u), h1=1.0, h2=0.0, assemble=False))
+        ref = O.ax_local(u.reshape(Lo.x.shape), Lo.G, Lo.B, Lo.D).ravel()
+        assert relmax(w, ref) < 1e-12
+
+
+def test_ax_full_size_sampled():
+    """The 32^3, N=7 warped Helmholtz workload: local Ax on sampled elements and the
+    assembled result at their nodes, against the oracle evaluated on the sample's
+    element neighbourhood only."""
+    dev()
+    mesh = si.box_mesh(32, 7, warp=0.1, perm_seed=0)
+    ctx = ctx_for(mesh, prec_copies=0, mg_orders=[7])
+    u = si.uniform_field(mesh, 0)
+    ut = T(u)
+    wl = H(ctx.ax(ut, h1=1.0, h2=0.5, assemble=False)).reshape(mesh["E"], -1)
+    wa = H(ctx.ax(ut, h1=1.0, h2=0.5, assemble=True)).reshape(mesh["E"], -1)
+    rng = np.random.default_rng(0)
+    sample = rng.choice(mesh["E"], 24, replace=False)
+    # neighbourhood: every element sharing a node with the sample
+    gid = mesh["gid"].reshape(mesh["E"], -1)
+    sgids = np.unique(gid[sample])
+    hood = np.flatnonzero(np.isin(gid, sgids).any(axis=1))
+    sub = {k: mesh[k][hood] for k in ("x", "y", "z")}
+    G, B, _ = O.geometry(sub["x"], sub["y"], sub["z"], 7)
+    D = O.deriv_matrix(7)
+    wref = O.ax_local(u[hood], G, B, D, 1.0, 0.5).reshape(hood.size, -1)
+    pos = {e: i for i, e in enumerate(hood)}
+    for e in sample:
+        assert relmax(wl[e], wref[pos[e]]) < 1e-12
+    # assembled: sum the oracle's local results over all copies inside the neighbourhood
+    flat_g = gid[hood].ravel()
+    sums = {}
+    np.add.at(sums_arr := np.zeros(flat_g.max() + 1), flat_g, wref.ravel())
+    dm = mesh["dirichlet"].reshape(mesh["E"], -1)
+    for e in sample:
+        ref = np.where(dm[e], 0.0, sums_arr[gid[e]])
+        assert relmax(wa[e], ref) < 1e-12
