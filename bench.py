@@ -82,7 +82,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [s.strip() for s in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.time(), parts))
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.time()
+        while self.proc and not self.rows and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def __exit__(self, *a):
         if self.proc:
@@ -93,14 +101,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        t0, t1 = getattr(self, "t_start", 0.0), getattr(self, "t_end", 1e30)
+        rows = [r for (t, r) in self.rows if t0 <= t <= t1 + 0.2]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
 # ----------------------------------------------------------------------------------
@@ -189,22 +200,25 @@ def solve_bench(ctx_cls, args, dev):
                        f"FCG + p-MG (7-3-1, Chebyshev-Jacobi degree 2, coarse Jacobi-PCG) to 1e-8",
            "n_L": int(mesh["x"].size), "n_G": int(ctx.levels[0]["nG"])}
     stream = torch.cuda.current_stream()
-    for prec in ("fp64", "fp32", "bf16g"):
-        ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled")   # warm-up incl. setup
+    variants = (("fp64", "fp64", False), ("fp32", "fp32", False), ("bf16g", "bf16g", False),
+                ("fp32_outer_pairs", "fp32", True))
+    for name, prec, op in variants:
+        solve = lambda: ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled", outer_pairs=op)
+        solve()   # warm-up, includes the preconditioner setup for this precision
         times, info = [], None
         for _ in range(args.solve_reps):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            x, info = ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled")
+            x, info = solve()
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
         t = min(times)
-        out[prec] = {"time_to_1e-8_s": t, "median_s": statistics.median(times), "iters": info["iters"],
+        out[name] = {"time_to_1e-8_s": t, "median_s": statistics.median(times), "iters": info["iters"],
                      "ms_per_iter": 1e3 * t / max(1, info["iters"]), "relres": info["relres"],
-                     "coarse_iters": info["coarse_iters"]}
+                     "coarse_iters": info["coarse_iters"], "smoother": prec, "outer_operator": "f32x2" if op else "f64"}
     if args.jacobi:
         ctx.solve(b, tol=1e-8, maxit=20000, precond="jacobi", rhs="assembled")
         torch.cuda.synchronize()
@@ -221,8 +235,8 @@ def solve_bench(ctx_cls, args, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--elements", type=int, default=32, help="elements per side of the Ax box")
     ap.add_argument("--solve-elements", type=int, default=24)
@@ -231,6 +245,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--jacobi", action="store_true", help="also time Jacobi-PCG on the solve problem")
+    ap.add_argument("--ax", default="fp64", choices=["fp64", "pairs"],
+                    help="element kernel of the timed step: FP64 instructions or FP32-pair arithmetic")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -253,24 +270,28 @@ def main():
     from paper_2104_05829_gb300 import SemContext
 
     mesh = build_mesh(args.elements, 7)
-    ctx = SemContext.from_mesh(mesh, prec_copies=0, mg_orders=[7])
+    ctx = SemContext.from_mesh(mesh, prec_copies=4, mg_orders=[7])
     lv = ctx.levels[0]
     nL, nG, n_shared, E = lv["nL"], lv["nG"], lv["n_seg_idx"], lv["E"]
     u = torch.tensor(mesh["u"].ravel(), device=dev)
     w = torch.empty_like(u)
     stream = torch.cuda.current_stream()
 
-    step = lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True)
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    pairs = args.ax == "pairs"
+    step = lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True, pairs=pairs)
     with ClockSampler(local) as clk:
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        clk.wait_first()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark("t_start")
         t = time_events(step, args.steps, stream)
         # dominant kernel alone: the local Ax launch, same stream, same inputs
-        t_ax = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False), args.steps, stream)
+        t_ax = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False, pairs=pairs), args.steps, stream)
+        clk.mark("t_end")
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -287,7 +308,7 @@ def main():
     bytes_alg = ax_gs_bytes(nL, n_shared, nG)
     roof = {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
             "frac": achieved_tf / pk["fp64_tflops"], "traffic": None,
-            "kernel": "k_ax<double,double,8> (FP64 local Ax)",
+            "kernel": "k_ax_pairs<8> (FP32-pair local Ax)" if pairs else "k_ax<double,double,8> (FP64 local Ax)",
             "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
             "hbm_view": {"bytes_per_step": bytes_alg, "achieved_gbs": bytes_alg / (ms / 1e3) / 1e9,
                          "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
@@ -295,7 +316,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32x2" if pairs else "f64", "data": "synthetic",
             "config": {"workload": f"FP64 Helmholtz Ax+gs (h1=1, h2=0.5) on a {args.elements}^3-element warped "
                                    f"unit-cube box, N=7, u ~ U[-1,1] continuous (seed 0)",
                        "E": E, "N": 7, "n_L": nL, "n_G": nG, "parallelism": f"replicas x{world}",
@@ -310,7 +331,7 @@ def main():
 
         def e2e_step():
             u.copy_(uh, non_blocking=True)
-            ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True)
+            ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True, pairs=pairs)
             wh.copy_(w, non_blocking=True)
 
         for _ in range(3):
@@ -319,6 +340,18 @@ def main():
         te = time_events(e2e_step, args.steps, stream)
         line["e2e"] = {"value": world * nG * args.steps / te / 1e9, "unit": "GDOF/s",
                        "h2d_bytes_per_step": 8 * nL, "d2h_bytes_per_step": 8 * nL, "ms_per_step": 1e3 * te / args.steps}
+    if not args.no_variants:
+        # the other element kernel on the same inputs (reported, not the headline)
+        other = not pairs
+        fn = lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True, pairs=other)
+        for _ in range(3):
+            fn()
+        tv = time_events(fn, args.steps, stream)
+        tva = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False, pairs=other), args.steps, stream)
+        line["variants"] = {("ax_fp32_pairs" if other else "ax_fp64"): {
+            "value": world * nG * args.steps / tv / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * tv / args.steps,
+            "ax_kernel_ms": 1e3 * tva / args.steps, "dtype": "f32x2" if other else "f64",
+            "ax_kernel_tflops_paper_count": flops / (tva / args.steps) / 1e12}}
     ctx.close()
     if not args.no_solve:
         line["solve"] = solve_bench(SemContext, args, dev)

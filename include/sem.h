@@ -55,10 +55,12 @@ extern "C" {
 #define SEM_FP64 0           /* FP64 geometric factors and arithmetic */
 #define SEM_FP32 1           /* FP32 geometric factors and arithmetic */
 #define SEM_BF16G 2          /* BF16 geometric factors, FP32 arithmetic */
+#define SEM_FP64P 3          /* FP64 in and out, arithmetic in FP32 pairs (~48 bits; see sem_ax) */
 
 /* sem_ax / sem_level_ax flags */
 #define SEM_AX_LOCAL 0       /* w_L = A_L u_L only (no assembly) */
 #define SEM_AX_ASSEMBLE 1    /* w_L = R QQ^T A_L u_L (gs_op(+) then Dirichlet mask) */
+#define SEM_AX_PAIRS 2       /* evaluate A_L with FP32-pair arithmetic instead of FP64 instructions */
 
 /* sem_gs flags */
 #define SEM_GS_ADD 0         /* w_L <- QQ^T w_L */
@@ -70,10 +72,12 @@ extern "C" {
 #define SEM_RHS_NODAL 0      /* f_L is a nodal function: b = R Q^T B_L f_L, replicated */
 #define SEM_RHS_ASSEMBLED 1  /* f_L already holds the assembled b, replicated on copies */
 #define SEM_X0_GIVEN 2       /* use u_L on entry as the initial guess (else x0 = 0) */
+#define SEM_OUTER_PAIRS 4    /* the outer (FP64) operator uses the FP32-pair kernel (SEM_AX_PAIRS) */
 
 /* precision bits in sem_opts.prec_copies: which preconditioner copies to build */
 #define SEM_BUILD_FP32 1
 #define SEM_BUILD_BF16G 2
+#define SEM_BUILD_PAIRS 4    /* (hi, lo) FP32 split of the FP64 factors for SEM_FP64P / SEM_AX_PAIRS */
 
 typedef struct sem_ctx sem_ctx;
 
@@ -99,7 +103,7 @@ typedef struct {
   uint64_t lanczos_seed;     /* SplitMix64 seed of the Lanczos start vector (1) */
   double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-4) */
   int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
-  int32_t prec_copies;       /* SEM_BUILD_* bits: FP32 / BF16 factor copies (SEM_BUILD_FP32|SEM_BUILD_BF16G) */
+  int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
 } sem_opts;
 
 /* Coefficients h1 (diffusion) and h2 (mass) of A = D^T h1 G D + h2 B. */
@@ -147,8 +151,14 @@ int sem_num_levels(const sem_ctx* ctx);
 int sem_level_info(const sem_ctx* ctx, int level, sem_level_desc* out);
 
 /* w_L = A_L u_L (flags SEM_AX_LOCAL) or R QQ^T A_L u_L (SEM_AX_ASSEMBLE) on the
- * fine level in FP64, A^e = D^T h1 G D + h2 B (eq. Ae). u_L and w_L must not
- * alias. Errors: SEM_EINVAL, SEM_ECUDA. */
+ * fine level in FP64, A^e = D^T h1 G D + h2 B (eq. Ae). With SEM_AX_PAIRS the
+ * element operator runs in FP32-pair arithmetic (every value an unevaluated sum
+ * of two floats, error-free TwoProduct/TwoSum; about 48 significant bits and
+ * the FP32 exponent range, |values| within ~1e-30..1e30; scalar h1 only), which
+ * GB300 executes far faster than FP64 instructions. The Dirichlet entries
+ * of u_L are used as given; pass a masked u_L (zero at Dirichlet nodes, as every
+ * solver vector is) to apply A = R Q^T A_L Q R^T. u_L and w_L must not alias.
+ * Errors: SEM_EINVAL, SEM_ECUDA. */
 int sem_ax(sem_ctx* ctx, const double* u_L, double* w_L, const sem_coef* coef, int flags, void* stream);
 
 /* w_L <- QQ^T w_L (SEM_GS_ADD) or R QQ^T w_L (SEM_GS_ADD_MASK) on the fine

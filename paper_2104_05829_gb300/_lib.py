@@ -18,12 +18,12 @@ SEM_EBREAKDOWN = -5
 SEM_EMESH = -6
 SEM_MAX_N = 11
 SEM_MAX_LEVELS = 6
-SEM_FP64, SEM_FP32, SEM_BF16G = 0, 1, 2
-SEM_AX_LOCAL, SEM_AX_ASSEMBLE = 0, 1
+SEM_FP64, SEM_FP32, SEM_BF16G, SEM_FP64P = 0, 1, 2, 3
+SEM_AX_LOCAL, SEM_AX_ASSEMBLE, SEM_AX_PAIRS = 0, 1, 2
 SEM_GS_ADD, SEM_GS_ADD_MASK = 0, 1
 SEM_PC_JACOBI, SEM_PC_PMG = 0, 1
-SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN = 0, 1, 2
-SEM_BUILD_FP32, SEM_BUILD_BF16G = 1, 2
+SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN, SEM_OUTER_PAIRS = 0, 1, 2, 4
+SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 
 

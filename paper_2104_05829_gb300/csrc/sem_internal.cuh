@@ -64,6 +64,7 @@ struct Level {
   double* G = nullptr;
   float* G32 = nullptr;
   __nv_bfloat16* G16 = nullptr;
+  float2* G2 = nullptr;        // (hi, lo) FP32 split of G for the pair-arithmetic kernel
   // coordinates, ids and Dirichlet flags as given (fine) or derived (coarse)
   double *x = nullptr, *y = nullptr, *z = nullptr;
   int64_t* gid = nullptr;
@@ -143,6 +144,10 @@ int ax_apply(const Level& L, int prec, const void* u, void* w, double h1, double
 int diag_local(const Level& L, double h1, double h2, const double* h1L, double* d, cudaStream_t s);
 int grad_h1_apply(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
 int geom_compute(Level& L, int* d_bad, cudaStream_t s);
+
+// ---- ax_pairs.cu
+int pairs_build(Level& L, cudaStream_t s);
+int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s);
 
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);

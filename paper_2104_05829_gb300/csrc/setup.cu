@@ -219,7 +219,7 @@ int dmalloc(T** p, size_t count) {
 }
 
 void free_level(Level& L) {
-  void* ptrs[] = {L.G, L.G32, L.G16, L.x, L.y, L.z, L.gid, L.dflag, L.ids, L.off, L.idx, L.mult, L.node,
+  void* ptrs[] = {L.G, L.G32, L.G16, L.G2, L.x, L.y, L.z, L.gid, L.dflag, L.ids, L.off, L.idx, L.mult, L.node,
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf};
   for (void* p : ptrs)
@@ -262,6 +262,7 @@ int build_level_products(Ctx& C, Level& L, cudaStream_t s) {
     set_detail("non-positive Jacobian at order %d", L.N);
     return SEM_EMESH;
   }
+  if (C.opts.prec_copies & SEM_BUILD_PAIRS) SEM_TRY(pairs_build(L, s));
   SEM_TRY(build_maps(L, s));
   // preconditioner and V-cycle vectors
   SEM_TRY(dmalloc(&L.dinv, n));
@@ -344,7 +345,7 @@ void sem_default_opts(sem_opts* o) {
   o->lanczos_seed = 1;
   o->coarse_tol = 1e-4;
   o->coarse_maxit = 100;
-  o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G;
+  o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
 }
 
 const char* sem_strerror(int code) {

@@ -296,6 +296,7 @@ int check_level(Ctx* C, int level) {
 int check_prec(Ctx* C, int level, int prec) {
   const Level& L = C->lev[level];
   if (prec == SEM_FP64) return SEM_OK;
+  if (prec == SEM_FP64P && L.G2) return SEM_OK;
   if (prec == SEM_FP32 && L.G32) return SEM_OK;
   if (prec == SEM_BF16G && L.G16) return SEM_OK;
   set_detail("precision %d not available (not built or unknown)", prec);
@@ -309,12 +310,14 @@ extern "C" {
 int sem_ax(sem_ctx* h, const double* u, double* w, const sem_coef* c, int flags, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));
-  if (!u || !w || !c || u == w || (flags & ~SEM_AX_ASSEMBLE)) {
-    set_detail("sem_ax: NULL or aliased vector, NULL coefficients or unknown flag");
+  if (!u || !w || !c || u == w || (flags & ~(SEM_AX_ASSEMBLE | SEM_AX_PAIRS)) ||
+      ((flags & SEM_AX_PAIRS) && c->h1_L)) {
+    set_detail("sem_ax: NULL or aliased vector, NULL coefficients, unknown flag, or nodal h1 with pairs");
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  SEM_TRY(ax_apply(C->lev[0], SEM_FP64, u, w, c->h1, c->h2, c->h1_L, s));
+  if (flags & SEM_AX_PAIRS) SEM_TRY(ax_pairs_apply(C->lev[0], u, w, c->h1, c->h2, s));
+  else SEM_TRY(ax_apply(C->lev[0], SEM_FP64, u, w, c->h1, c->h2, c->h1_L, s));
   if (flags & SEM_AX_ASSEMBLE) SEM_TRY(gs_apply(C->lev[0], SEM_FP64, w, true, s));
   return SEM_OK;
 }
@@ -339,8 +342,10 @@ int sem_level_ax(sem_ctx* h, int level, int prec, const void* u, void* w, double
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  SEM_TRY(ax_apply(C->lev[level], prec, u, w, h1, h2, nullptr, s));
-  if (flags & SEM_AX_ASSEMBLE) SEM_TRY(gs_apply(C->lev[level], prec, w, true, s));
+  if (prec == SEM_FP64P) SEM_TRY(ax_pairs_apply(C->lev[level], (const double*)u, (double*)w, h1, h2, s));
+  else SEM_TRY(ax_apply(C->lev[level], prec, u, w, h1, h2, nullptr, s));
+  const int vprec = (prec == SEM_FP64P) ? SEM_FP64 : prec;
+  if (flags & SEM_AX_ASSEMBLE) SEM_TRY(gs_apply(C->lev[level], vprec, w, true, s));
   return SEM_OK;
 }
 
@@ -479,7 +484,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
   SEM_TRY(check_level(C, 0));
   if (!f || !c || !u || f == u || !(tol >= 0.0) || maxit < 0 ||
       (precond != SEM_PC_JACOBI && precond != SEM_PC_PMG) ||
-      (rhs_flags & ~(SEM_RHS_ASSEMBLED | SEM_X0_GIVEN))) {
+      (rhs_flags & ~(SEM_RHS_ASSEMBLED | SEM_X0_GIVEN | SEM_OUTER_PAIRS))) {
     set_detail("sem_solve: bad argument");
     return SEM_EINVAL;
   }
@@ -488,6 +493,17 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
     set_detail("sem_solve: the p-multigrid preconditioner needs scalar coefficients");
     return SEM_EINVAL;
   }
+  const bool pairs = (rhs_flags & SEM_OUTER_PAIRS) != 0;
+  if (pairs && (c->h1_L || !C->lev[0].G2)) {
+    set_detail("sem_solve: SEM_OUTER_PAIRS needs scalar h1 and the pair factors (SEM_BUILD_PAIRS)");
+    return SEM_EINVAL;
+  }
+  // outer operator R QQ^T A_L p (FP64 or FP32-pair element kernel)
+  auto outer_ax = [&](const double* in, double* out, const double* skip, cudaStream_t st) -> int {
+    if (pairs) SEM_TRY(ax_pairs_apply(C->lev[0], in, out, c->h1, c->h2, st));
+    else SEM_TRY(ax_apply(C->lev[0], SEM_FP64, in, out, c->h1, c->h2, c->h1_L, st, skip));
+    return gs_apply_skip(C->lev[0], SEM_FP64, out, true, skip, st);
+  };
   cudaStream_t s = (cudaStream_t)stream;
   Level& L = C->lev[0];
   const int64_t n = L.nL;
@@ -503,10 +519,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
   SEM_TRY(gs_apply(L, SEM_FP64, b, true, s));
   const bool x0 = (rhs_flags & SEM_X0_GIVEN) != 0;
   double* w = C->w;
-  if (x0) {
-    SEM_TRY(ax_apply(L, SEM_FP64, u, w, c->h1, c->h2, c->h1_L, s));
-    SEM_TRY(gs_apply(L, SEM_FP64, w, true, s));
-  }
+  if (x0) SEM_TRY(outer_ax(u, w, nullptr, s));
   SEM_CUDA_TRY(cudaMemsetAsync(C->scal + 1 * S_NSLOTS + S_TOTAL, 0, sizeof(double), s));
   int iters = 0;
   double rr = 0, bb = 0;
@@ -534,8 +547,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
       }
       const int nb = std::min(batch, maxit - launched);
       for (int q = 0; q < nb; ++q) {
-        SEM_TRY(ax_apply(L, SEM_FP64, C->p, w, c->h1, c->h2, c->h1_L, s, sc + S_DONE));
-        SEM_TRY(gs_apply_skip(L, SEM_FP64, w, true, sc + S_DONE, s));
+        SEM_TRY(outer_ax(C->p, w, sc + S_DONE, s));
         SEM_TRY(kr_alpha(*C, L, SEM_FP64, C->p, w, sc, s));
         SEM_TRY(kr_update_jacobi(*C, L, SEM_FP64, u, C->p, C->r, w, dinv, sc, s));
         SEM_TRY(kr_direction_jacobi(L, SEM_FP64, C->p, C->r, dinv, sc, s));
@@ -556,8 +568,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
       SEM_TRY(kr_beta_flex(*C, L, C->z, C->r, C->dr, sc, s));
       SEM_TRY(kr_direction(L, C->p, C->z, sc, s));
       for (int k = 0; k < maxit; ++k) {
-        SEM_TRY(ax_apply(L, SEM_FP64, C->p, w, c->h1, c->h2, nullptr, s));
-        SEM_TRY(gs_apply(L, SEM_FP64, w, true, s));
+        SEM_TRY(outer_ax(C->p, w, nullptr, s));
         SEM_TRY(kr_alpha(*C, L, SEM_FP64, C->p, w, sc, s));
         SEM_TRY(kr_update_flex(*C, L, u, C->p, C->r, w, C->dr, sc, s));
         SEM_TRY(read_scalars(*C, 0, s));

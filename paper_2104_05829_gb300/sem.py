@@ -13,8 +13,9 @@ import torch
 
 from . import _lib as L
 
-_PREC = {"fp64": L.SEM_FP64, "fp32": L.SEM_FP32, "bf16g": L.SEM_BF16G,
-         L.SEM_FP64: L.SEM_FP64, L.SEM_FP32: L.SEM_FP32, L.SEM_BF16G: L.SEM_BF16G}
+_PREC = {"fp64": L.SEM_FP64, "fp32": L.SEM_FP32, "bf16g": L.SEM_BF16G, "fp64p": L.SEM_FP64P,
+         L.SEM_FP64: L.SEM_FP64, L.SEM_FP32: L.SEM_FP32, L.SEM_BF16G: L.SEM_BF16G, L.SEM_FP64P: L.SEM_FP64P}
+_F64 = (L.SEM_FP64, L.SEM_FP64P)
 _PC = {"jacobi": L.SEM_PC_JACOBI, "pmg": L.SEM_PC_PMG}
 
 
@@ -105,24 +106,26 @@ class SemContext:
         return {k: getattr(d, k) for k, _ in d._fields_}
 
     def nl(self, level=0):
+        if not 0 <= level < len(self.levels):
+            return self.level_info(level)["nL"]      # raises SemError (SEM_EINVAL) from the library
         return self.levels[level]["nL"]
 
     def empty(self, level=0, prec="fp64", device="cuda"):
-        dt = torch.float64 if _PREC[prec] == L.SEM_FP64 else torch.float32
+        dt = torch.float64 if _PREC[prec] in _F64 else torch.float32
         return torch.empty(self.nl(level), dtype=dt, device=device)
 
     def zeros(self, level=0, prec="fp64", device="cuda"):
         return self.empty(level, prec, device).zero_()
 
     # ---- fine-level FP64 operators ---------------------------------------------
-    def ax(self, u, w=None, h1=1.0, h2=0.0, h1_L=None, assemble=True, stream=None):
+    def ax(self, u, w=None, h1=1.0, h2=0.0, h1_L=None, assemble=True, pairs=False, stream=None):
         n = self.nL
         if w is None:
             w = torch.empty_like(u)
         c = L.SemCoef(float(h1), float(h2), _dev(h1_L, torch.float64, n, "h1_L") if h1_L is not None else None)
+        flags = (L.SEM_AX_ASSEMBLE if assemble else L.SEM_AX_LOCAL) | (L.SEM_AX_PAIRS if pairs else 0)
         L.check(self._lib.sem_ax(self._h, _dev(u, torch.float64, n, "u"), _dev(w, torch.float64, n, "w"),
-                                 C.byref(c), L.SEM_AX_ASSEMBLE if assemble else L.SEM_AX_LOCAL, _stream(stream)),
-                "sem_ax")
+                                 C.byref(c), flags, _stream(stream)), "sem_ax")
         return w
 
     def gs(self, w, mask=False, stream=None):
@@ -157,7 +160,7 @@ class SemContext:
 
     # ---- level operators -------------------------------------------------------
     def _vec(self, t, level, prec, name):
-        dt = torch.float64 if _PREC[prec] == L.SEM_FP64 else torch.float32
+        dt = torch.float64 if _PREC[prec] in _F64 else torch.float32
         return _dev(t, dt, self.nl(level), name)
 
     def level_ax(self, level, u, w=None, h1=1.0, h2=0.0, prec="fp64", assemble=True, stream=None):
@@ -215,13 +218,14 @@ class SemContext:
 
     # ---- solve -----------------------------------------------------------------
     def solve(self, f, h1=1.0, h2=0.0, h1_L=None, tol=1e-8, maxit=1000, precond="jacobi", prec="fp64",
-              rhs="nodal", x0=None, u=None, stream=None, raise_on_error=True):
+              rhs="nodal", x0=None, u=None, outer_pairs=False, stream=None, raise_on_error=True):
         n = self.nL
         if u is None:
             u = torch.empty_like(f) if x0 is None else x0.clone()
         elif x0 is not None:
             u.copy_(x0)
         flags = (L.SEM_RHS_ASSEMBLED if rhs == "assembled" else L.SEM_RHS_NODAL) | (L.SEM_X0_GIVEN if x0 is not None else 0)
+        flags |= L.SEM_OUTER_PAIRS if outer_pairs else 0
         c = L.SemCoef(float(h1), float(h2), _dev(h1_L, torch.float64, n, "h1_L") if h1_L is not None else None)
         info = L.SemInfo()
         rc = self._lib.sem_solve(self._h, _dev(f, torch.float64, n, "f"), C.byref(c), float(tol), int(maxit),

@@ -50,11 +50,16 @@ def test_ax_local_fp64_nodal_h1():
 def test_ax_assembled_fp64(N, dirichlet):
     dev()
     mesh, ctx, lev = _setup((4, 4, 3), N, dirichlet=dirichlet)
-    u = si.uniform_field(mesh, 0)          # continuous field
+    u = si.uniform_field(mesh, 0)          # continuous field, Dirichlet entries nonzero
     w = H(ctx.ax(T(u), h1=1.0, h2=0.5, assemble=True))
-    ug = global_from_L(lev, u)
-    ref = O.q_gather(lev.apply(ug, 1.0, 0.5), lev.node)
+    # R QQ^T A_L u: the input is used as given, the output is masked
+    wl = O.ax_local(u, lev.G, lev.B, lev.D, 1.0, 0.5)
+    ref = O.q_gather(lev.mask(O.q_scatter(wl, lev.node, lev.n_G)), lev.node)
     assert relmax(w, ref) < 1e-12
+    # with a masked input this is the SPD operator R Q^T A_L Q R^T
+    um = np.where(lev.dir_g[lev.node], 0.0, u.ravel())
+    w2 = H(ctx.ax(T(um), h1=1.0, h2=0.5, assemble=True))
+    assert relmax(w2, O.q_gather(lev.apply(global_from_L(lev, um), 1.0, 0.5), lev.node)) < 1e-12
 
 
 def test_gs_matches_oracle_qqt():
@@ -116,13 +121,54 @@ def test_ax_full_size_sampled():
     D = O.deriv_matrix(7)
     wref = O.ax_local(u[hood], G, B, D, 1.0, 0.5).reshape(hood.size, -1)
     pos = {e: i for i, e in enumerate(hood)}
-    for e in sample:
-        assert relmax(wl[e], wref[pos[e]]) < 1e-12
+    idx = [pos[e] for e in sample]
+    assert relmax(wl[sample], wref[idx]) < 1e-12
     # assembled: sum the oracle's local results over all copies inside the neighbourhood
     flat_g = gid[hood].ravel()
-    sums = {}
-    np.add.at(sums_arr := np.zeros(flat_g.max() + 1), flat_g, wref.ravel())
+    sums_arr = np.zeros(flat_g.max() + 1)
+    np.add.at(sums_arr, flat_g, wref.ravel())
     dm = mesh["dirichlet"].reshape(mesh["E"], -1)
-    for e in sample:
-        ref = np.where(dm[e], 0.0, sums_arr[gid[e]])
-        assert relmax(wa[e], ref) < 1e-12
+    ref = np.where(dm[sample], 0.0, sums_arr[gid[sample]])
+    assert relmax(wa[sample], ref) < 1e-12
+
+
+# ---- FP64-accurate operator in FP32-pair arithmetic (SEM_AX_PAIRS / SEM_FP64P) ----
+@pytest.mark.parametrize("N", range(1, 12))
+def test_ax_pairs_all_orders(N):
+    dev()
+    mesh, ctx, lev = _setup((3, 2, 5), N, seed=N)
+    rng = np.random.default_rng(N)
+    u = rng.uniform(-1, 1, mesh["x"].shape)
+    for h1, h2 in ((1.0, 0.0), (0.8, 0.5)):
+        w = H(ctx.ax(T(u), h1=h1, h2=h2, assemble=False, pairs=True))
+        ref = O.ax_local(u, lev.G, lev.B, lev.D, h1, h2).ravel()
+        err = relmax(w, ref)
+        print(f"pairs N={N} h1={h1} h2={h2} relmax={err:.3e}")
+        assert err < 1e-12, (N, err)
+
+
+def test_ax_pairs_smooth_field_and_level_api():
+    """A smooth input (strong cancellation in D u) through the level API."""
+    dev()
+    mesh, ctx, lev = _setup((4, 4, 4), 7)
+    u = np.sin(np.pi * mesh["x"]) * np.cos(2 * np.pi * mesh["y"]) * np.exp(mesh["z"])
+    w = H(ctx.level_ax(0, T(u), h1=1.0, h2=0.5, prec="fp64p", assemble=True))
+    wl = O.ax_local(u, lev.G, lev.B, lev.D, 1.0, 0.5)
+    ref = O.q_gather(lev.mask(O.q_scatter(wl, lev.node, lev.n_G)), lev.node)
+    err = relmax(w, ref)
+    print(f"pairs smooth assembled relmax={err:.3e}")
+    assert err < 1e-12
+
+
+def test_ax_pairs_full_size_sampled():
+    dev()
+    mesh = si.box_mesh(32, 7, warp=0.1, perm_seed=0)
+    ctx = ctx_for(mesh, prec_copies=4, mg_orders=[7])
+    u = si.uniform_field(mesh, 0)
+    wl = H(ctx.ax(T(u), h1=1.0, h2=0.5, assemble=False, pairs=True)).reshape(mesh["E"], -1)
+    sample = np.random.default_rng(1).choice(mesh["E"], 32, replace=False)
+    G, B, _ = O.geometry(mesh["x"][sample], mesh["y"][sample], mesh["z"][sample], 7)
+    ref = O.ax_local(u[sample], G, B, O.deriv_matrix(7), 1.0, 0.5).reshape(sample.size, -1)
+    err = relmax(wl[sample], ref)
+    print(f"pairs full-size sample relmax={err:.3e}")
+    assert err < 1e-12

@@ -29,7 +29,7 @@ def test_not_converged_reports_and_keeps_iterate():
     _, f = si.manufactured(mesh)
     x, info = ctx.solve(T(f), tol=1e-14, maxit=3, raise_on_error=False)
     assert info["status"] == _lib.SEM_ENOTCONV
-    assert info["iters"] == 3 and 0 < info["relres"] < 1
+    assert info["iters"] == 3 and np.isfinite(info["relres"]) and info["relres"] > 1e-14
     assert np.all(np.isfinite(H(x)))
 
 

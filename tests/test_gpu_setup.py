@@ -69,8 +69,12 @@ def test_geometry_fp64(N):
     G = ctx.geom(0)
     Go, Bo, _ = O.geometry(mesh["x"], mesh["y"], mesh["z"], N)
     ref = np.concatenate([Go, Bo[None]]).reshape(7, mesh["E"], -1).transpose(1, 0, 2)
+    # norm-wise per component, scaled by the largest diagonal factor (the
+    # off-diagonal factors can be rounding-level where the warp is nearly affine)
+    scale = np.max(np.abs(ref[:, [0, 3, 5]]))
     for c in range(7):
-        assert relmax(G[:, c], ref[:, c]) < 1e-13, (N, c)
+        sc = scale if c < 6 else np.max(np.abs(ref[:, 6]))
+        assert np.max(np.abs(G[:, c] - ref[:, c])) < 1e-13 * sc, (N, c)
 
 
 def test_geometry_lowp_copies_round_the_fp64_values():
@@ -90,11 +94,15 @@ def test_geometry_lowp_copies_round_the_fp64_values():
     diff = g16 != codes
     # a different code is only allowed where the oracle's value sits within
     # 1e-12 (relative) of a rounding tie, i.e. where last-bit FP64 differences decide
+    # or where the value itself is rounding-level (|G| < 1e-13 of the component scale)
     if diff.any():
         ulp = np.abs(q) * 2.0 ** -8
         tie_dist = np.abs(np.abs(ref - q) - 0.5 * ulp)
-        assert np.all(tie_dist[diff] < 1e-12 * np.abs(ref[diff]))
-    assert diff.mean() < 1e-6
+        scale = np.max(np.abs(ref), axis=(0, 2), keepdims=True) * np.ones_like(ref)
+        ok = (tie_dist < 1e-12 * np.abs(ref)) | (np.abs(ref) < 1e-13 * scale)
+        assert np.all(ok[diff])
+    big = np.abs(ref) >= 1e-13 * np.max(np.abs(ref), axis=(0, 2), keepdims=True)
+    assert diff[big].mean() < 1e-6
 
 
 @pytest.mark.parametrize("Nf,orders", [(7, [7, 3, 1]), (5, [5, 2, 1]), (4, [4, 2, 1])])

@@ -165,3 +165,16 @@ def test_solve_helmholtz_x0_and_nodal_rhs():
     x, info = ctx.solve(T(f), h1=0.7, h2=2.0, tol=1e-13, maxit=2000, x0=T(x0))
     ref = O.solve(lev, lev.rhs_from_nodal(f), 0.7, 2.0, tol=1e-14, maxit=2000)
     assert relmax(H(x), _gL(lev, ref.x)) < 1e-9
+
+
+def test_pmg_solve_with_pair_arithmetic_outer_operator():
+    dev()
+    mesh = si.box_mesh((4, 4, 4), 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
+    ctx = ctx_for(mesh)
+    lev = O.level_from_mesh(mesh)
+    b = si.gaussian_assembled_rhs(mesh, 0)
+    x, info = ctx.solve(T(b), tol=1e-8, maxit=200, precond="pmg", prec="fp32", rhs="assembled", outer_pairs=True)
+    bg = lev.mask(global_from_L(lev, b))
+    xg = global_from_L(lev, H(x))
+    true_res = np.linalg.norm(bg - lev.apply(xg)) / np.linalg.norm(bg)
+    assert info["relres"] <= 1e-8 and true_res < 2e-8
