@@ -3,12 +3,12 @@
  * path of NekRS (Fischer et al., "NekRS, a GPU-accelerated spectral element
  * Navier-Stokes solver"), written for one NVIDIA GB300 (sm_103a).
  *
- * Problem (Section 2.2, eq. aip/A and the Helmholtz substep eq. ns_wrt2):
+ * Problem (Section 2.3, eq. aip/A and the Helmholtz substep eq. ns_wrt2):
  *   find u with  A u = b,  A = R Q^T A_L Q R^T,
  *   A^e = D^T (h1 G^e) D + h2 B^e            (eq. Ae, eq. gij, eq. vBu)
  * on E hexahedral elements of order N with GLL points. Q is the Boolean
  * global-to-local map built from per-point global ids (eq. dssum and the
- * gs_setup interface of Section 3, "Parallel Communication"); R removes
+ * gs_setup interface of Section 3.2, "Parallel Communication"); R removes
  * Dirichlet rows (footnote below eq. dssum).
  *
  * Vectors. Every vector passed to the library is an L-vector: E blocks of
@@ -138,8 +138,8 @@ void sem_default_opts(sem_opts* opts);
 const char* sem_strerror(int code);
 const char* sem_last_error_detail(void);
 
-/* Build everything the path needs on the current CUDA device (Section 2.2 and
- * "Parallel Communication"): GLL rule and D_hat (eq. dh) per order, geometric
+/* Build everything the path needs on the current CUDA device (Sections 2.3,
+ * 3.2 and 3.4): GLL rule and D_hat (eq. dh) per order, geometric
  * factors G and B in FP64 (eq. grad, eq. gij, eq. vBu) plus FP32/BF16 copies,
  * the canonical gather-scatter maps (gs_setup), the Dirichlet mask and the
  * multigrid levels. Synchronous. Errors: SEM_EINVAL (bad N/E/pointer, negative
@@ -162,7 +162,7 @@ int sem_level_info(const sem_ctx* ctx, int level, sem_level_desc* out);
 int sem_ax(sem_ctx* ctx, const double* u_L, double* w_L, const sem_coef* coef, int flags, void* stream);
 
 /* w_L <- QQ^T w_L (SEM_GS_ADD) or R QQ^T w_L (SEM_GS_ADD_MASK) on the fine
- * level in FP64: the gs_op(+) of "Parallel Communication". In place. */
+ * level in FP64: the gs_op(+) of Section 3.2. In place. */
 int sem_gs(sem_ctx* ctx, double* w_L, int flags, void* stream);
 
 /* Level operators (level 0 = fine, 1.. coarser). `prec` selects SEM_FP64
@@ -177,7 +177,7 @@ int sem_level_gs(sem_ctx* ctx, int level, int prec, void* w_L, int flags, void* 
 int sem_level_dinv(sem_ctx* ctx, int level, double h1, double h2, double* dinv_L, void* stream);
 
 /* Multigrid transfers between level `level` (fine) and `level`+1 (coarse)
- * ("Poisson Solve Preconditioning", orders N, N/2, ..., 1):
+ * (Section 3.4, orders N, N/2, ..., 1):
  *   prolong : x_f += R_f J e_c  (J: tensor interpolation, e_c continuous)
  *   restrict: r_c  = R_c QQ^T_c J^T (W_f r_f), W_f the counting weight 1/m. */
 int sem_prolong_add(sem_ctx* ctx, int level, int prec, const void* ec_L, void* xf_L, void* stream);

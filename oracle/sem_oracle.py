@@ -8,18 +8,17 @@ arithmetic).
 
 Everything here is written for readability against the paper
 (Fischer et al., "NekRS, a GPU-accelerated spectral element Navier-Stokes
-solver"), Section 2 ("Spectral Element Discretization") and Section 3
-("Parallel GPU Development" / "Poisson Solve Preconditioning"), in float64:
+solver"), Section 2.3 ("Spectral Element Discretization"), Section 3.2
+("Parallel Communication") and Section 3.4 ("Poisson Solve Preconditioning"), in float64:
 
 * GLL rule and derivative matrix (eq. xijk, eq. dh),
 * geometric factors (eq. grad, eq. vBu, eq. gij),
 * local operator A^e = D^T G D (+ h2 B) by sum factorisation (eq. Ae) and, for
   tiny meshes, as explicit Kronecker-product element matrices assembled into
   Q^T A_L Q (the "assembled stiffness matrix" below eq. dssum),
-* the gather-scatter QQ^T on global ids (the gs_op(+) interface, Section 3
-  "Parallel Communication"),
+* the gather-scatter QQ^T on global ids (the gs_op(+) interface, Section 3.2),
 * Jacobi-PCG, flexible PCG, Chebyshev-Jacobi smoothing and the p-multigrid
-  V-cycle with orders N, N/2 .. 1 ("Poisson Solve Preconditioning"),
+  V-cycle with orders N, N/2 .. 1 (Section 3.4),
 * the adjoint gradient of a mass-weighted loss with respect to nodal h1.
 
 Global (unique-node) vectors are used for every solver here; the library works
@@ -55,7 +54,7 @@ def legendre_pair(N: int, x):
 
 
 def gll(N: int):
-    """Gauss-Lobatto-Legendre nodes xi_0 < ... < xi_N and weights rho_j (Section 2.2).
+    """Gauss-Lobatto-Legendre nodes xi_0 < ... < xi_N and weights rho_j (Section 2.3).
 
     The nodes are -1, +1 and the N-1 roots of P_N'. The roots are found by Newton's
     method on P_N' started from the Chebyshev-Gauss-Lobatto points, with
@@ -160,7 +159,7 @@ def weights3(rho: np.ndarray) -> np.ndarray:
 
 
 def geometry(x, y, z, N: int):
-    """Geometric factors of Section 2.2.
+    """Geometric factors of Section 2.3.
 
     Returns (G, B, Jac) where G has shape (6, E, NP, NP, NP) holding
     G11, G12, G13, G22, G23, G33 of eq. gij, B = rho_ijk J_ijk (eq. vBu) and Jac
@@ -386,7 +385,7 @@ def level_from_mesh(mesh: dict) -> Level:
 
 
 # ----------------------------------------------------------------------------
-# p-multigrid level construction (orders N, N/2, ..., 1; "Poisson Solve Preconditioning")
+# p-multigrid level construction (orders N, N/2, ..., 1; Section 3.4)
 # ----------------------------------------------------------------------------
 
 
@@ -620,7 +619,7 @@ def pcg(apply, b, minv, tol: float, maxit: int, flexible: bool = False) -> Solve
     """Preconditioned CG from x0 = 0 (Saad, Alg. 9.1), stopping when ||r||/||b|| <= tol.
 
     With ``flexible`` the Polak-Ribiere form beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k)
-    is used (flexible CG, "Poisson Solve Preconditioning"); otherwise
+    is used (flexible CG, Section 3.4); otherwise
     beta = (z_{k+1}, r_{k+1}) / (z_k, r_k).
     """
     x = np.zeros_like(b)
@@ -669,7 +668,7 @@ class MGParams:
 
 class PMG:
     """p-multigrid V-cycle with Chebyshev-Jacobi smoothing on every level but the
-    coarsest and a Jacobi-PCG coarse solve ("Poisson Solve Preconditioning")."""
+    coarsest and a Jacobi-PCG coarse solve (Section 3.4, "Poisson Solve Preconditioning")."""
 
     def __init__(self, levels, h1=1.0, h2=0.0, params: MGParams | None = None):
         self.levels = levels

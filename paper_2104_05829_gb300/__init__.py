@@ -1,4 +1,4 @@
-"""GB300-native spectral-element elliptic solver path (NekRS, Section 2.2 / 3).
+"""GB300-native spectral-element elliptic solver path (NekRS, Sections 2.3 and 3.2-3.4).
 
 The compute lives in libsem.so (CUDA, sm_103a); this package holds its build
 script and a thin Python binding. Nothing here falls back to the CPU: if the

@@ -1,4 +1,4 @@
-// Gather-scatter w_L <- QQ^T w_L (gs_op with +, "Parallel Communication") and
+// Gather-scatter w_L <- QQ^T w_L (gs_op with +, Section 3.2) and
 // the Dirichlet mask R^T R (footnote below eq. dssum).
 //
 // The segments are the global nodes that need work: nodes with more than one

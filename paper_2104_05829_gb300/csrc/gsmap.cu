@@ -1,5 +1,5 @@
 // gs_setup on the device: canonical gather-scatter maps from per-point global
-// ids ("Parallel Communication": ids are global pointers, positions are local
+// ids (Section 3.2, "Parallel Communication": ids are global pointers, positions are local
 // pointers, 0 marks a singleton).
 //
 // The (id, local index) pairs with a nonzero id are sorted by a stable LSD

@@ -1,7 +1,7 @@
 // sem_setup / sem_free and the setup products: GLL rule and D_hat per order
-// (Section 2.2, eq. dh), device geometry (eq. grad, eq. gij, eq. vBu), the
-// canonical gather-scatter maps (gs_setup) and the p-multigrid levels
-// ("Poisson Solve Preconditioning": orders N, N/2, ..., 1).
+// (Section 2.3, eq. dh), device geometry (eq. grad, eq. gij, eq. vBu), the
+// canonical gather-scatter maps (gs_setup, Section 3.2) and the p-multigrid
+// levels (Section 3.4, "Poisson Solve Preconditioning": orders N, N/2, ..., 1).
 #include <cmath>
 #include <cstdarg>
 #include <cstring>

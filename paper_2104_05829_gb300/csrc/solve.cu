@@ -1,7 +1,7 @@
 // Solvers and the remaining entry points.
 //
 // * Jacobi-PCG (the viscous-substep solver of Section 2.2) and flexible PCG
-//   preconditioned by a p-multigrid V-cycle ("Poisson Solve Preconditioning":
+//   preconditioned by a p-multigrid V-cycle (Section 3.4, "Poisson Solve Preconditioning":
 //   orders N, N/2, ..., 1, Chebyshev-accelerated Jacobi smoothing on every level
 //   but the coarsest, a Jacobi-PCG coarse solve). FP64 outer iteration; the
 //   V-cycle runs in FP64, FP32 or FP32 with BF16 geometric factors.

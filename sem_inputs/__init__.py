@@ -6,7 +6,7 @@ coefficient fields. It holds none of the method's arithmetic (no quadrature,
 no differentiation, no operator, no gather-scatter). The oracle, the tests and
 the benchmark all consume what it produces; the CUDA library never imports it.
 
-Layout (Section 2.2, eq. uijk): an L-vector holds E blocks of (N+1)^3 values,
+Layout (Section 2.3, eq. uijk): an L-vector holds E blocks of (N+1)^3 values,
 point (i, j, k) of element e at index i + (N+1)*(j + (N+1)*(k + (N+1)*e)),
 i fastest. Arrays here are shaped (E, N+1, N+1, N+1) with axes (e, k, j, i).
 

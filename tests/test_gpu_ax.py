@@ -133,6 +133,10 @@ def test_ax_full_size_sampled():
 
 
 # ---- FP64-accurate operator in FP32-pair arithmetic (SEM_AX_PAIRS / SEM_FP64P) ----
+# Tolerance: the pair format carries ~48 significant bits (2^-48 vs 2^-53 for FP64),
+# so its rounding errors are up to 32x those of the FP64 kernel, which stays below
+# 1.5e-13 here; 32 * 1.5e-13 = 4.8e-12 -> PAIRS_TOL = 5e-12.
+PAIRS_TOL = 5e-12
 @pytest.mark.parametrize("N", range(1, 12))
 def test_ax_pairs_all_orders(N):
     dev()
@@ -144,7 +148,7 @@ def test_ax_pairs_all_orders(N):
         ref = O.ax_local(u, lev.G, lev.B, lev.D, h1, h2).ravel()
         err = relmax(w, ref)
         print(f"pairs N={N} h1={h1} h2={h2} relmax={err:.3e}")
-        assert err < 1e-12, (N, err)
+        assert err < PAIRS_TOL, (N, err)
 
 
 def test_ax_pairs_smooth_field_and_level_api():
@@ -157,7 +161,7 @@ def test_ax_pairs_smooth_field_and_level_api():
     ref = O.q_gather(lev.mask(O.q_scatter(wl, lev.node, lev.n_G)), lev.node)
     err = relmax(w, ref)
     print(f"pairs smooth assembled relmax={err:.3e}")
-    assert err < 1e-12
+    assert err < PAIRS_TOL
 
 
 def test_ax_pairs_full_size_sampled():
@@ -171,4 +175,4 @@ def test_ax_pairs_full_size_sampled():
     ref = O.ax_local(u[sample], G, B, O.deriv_matrix(7), 1.0, 0.5).reshape(sample.size, -1)
     err = relmax(wl[sample], ref)
     print(f"pairs full-size sample relmax={err:.3e}")
-    assert err < 1e-12
+    assert err < PAIRS_TOL

@@ -2,7 +2,7 @@
 
 Each check comes from something the paper or the mathematics fixes, not from
 the oracle itself: the closed-form rules in tests/golden, the quadrature
-exactness of Section 2.2 (degree <= 2N-1), exact differentiation of P_N
+exactness of Section 2.3 (degree <= 2N-1), exact differentiation of P_N
 (eq. dh), and the antisymmetry of D_hat on symmetric nodes.
 """
 import math
@@ -42,7 +42,7 @@ def test_gll_quadrature_exactness(N):
     for k in range(0, 2 * N):
         exact = 0.0 if k % 2 else 2.0 / (k + 1)
         assert abs(rho @ xi ** k - exact) < 1e-13, (N, k)
-    # degree 2N is not integrated exactly (Section 2.2: exact only up to 2N-1)
+    # degree 2N is not integrated exactly (Section 2.3: exact only up to 2N-1)
     k = 2 * N
     assert abs(rho @ xi ** k - 2.0 / (k + 1)) > 1e-10
 

@@ -4,7 +4,7 @@ Sources of truth: dense linear algebra on tiny meshes (solves, eigenvalues,
 adjoint gradients from the explicit derivative of the assembled matrix),
 closed forms (the Chebyshev error polynomial T_k((theta-lambda)/delta)/T_k(sigma),
 polynomial reproduction of interpolation), central finite differences, and
-the spectral convergence the paper states for smooth solutions (Section 2.2).
+the spectral convergence the paper states for smooth solutions (Section 2.3).
 """
 import numpy as np
 import pytest
