@@ -174,6 +174,20 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(t_local: float, units_local: float, dist=None, device="cpu"):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of all ranks' units."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return t_local, units_local
+    import torch
+
+    dist.barrier()
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def time_events(fn, steps, stream):
     import torch
 
@@ -293,13 +307,9 @@ def main():
         t_ax = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False, pairs=pairs), args.steps, stream)
         clk.mark("t_end")
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = tt.item()
+    t, units = aggregate(t, nG * args.steps, dist, dev)
     ms = 1e3 * t / args.steps
-    value = world * nG * args.steps / t / 1e9
+    value = units / t / 1e9
 
     pk = peaks()
     flops = ax_flops_per_element(7) * E
