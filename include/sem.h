@@ -224,6 +224,23 @@ int sem_mass_local(sem_ctx* ctx, const double* f_L, double* out_L, void* stream)
  * over one owner copy of each non-Dirichlet node. Result in *out (HOST). Synchronous. */
 int sem_dot(sem_ctx* ctx, const double* a_L, const double* b_L, double* out, void* stream);
 
+/* Dot product sum_l mask_l a_l b_l of two FP64 device vectors (mask: DEVICE
+ * uint8 flags, NULL = all ones) written to *out (DEVICE), that allocates no
+ * memory and needs no context. The paper has no counterpart: this is for
+ * callers that cannot allocate device memory (a host framework that owns a
+ * fixed device budget and passes only pointers into it, a latency-critical
+ * loop that must not meet cudaMalloc's device-wide synchronisation, a caller
+ * holding no sem_ctx). Its scratch is a file-scope static device array of
+ * 64 KiB + 4 bytes per device, held until the process exits. n may be at most
+ * 67,108,864; larger n returns SEM_EINVAL without launching anything. The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and must come before any stream capture on that device. Calls share the
+ * array: calls that overlap on the GPU (concurrent streams) race and must be
+ * serialised by the caller. Asynchronous on `stream`. To reproduce sem_dot's
+ * unique-node product pass the owner mask: 1 where label[l] == l and dmask[l] == 0
+ * (sem_get_maps). */
+int sem_dot_static(const double* a, const double* b, const uint8_t* mask, int64_t n, double* out, void* stream);
+
 /* ---- read-back of setup products, for validation (HOST outputs, synchronous) ---- */
 /* Canonical gather-scatter maps of `level` (any pointer may be NULL):
  * ids[n_ids]: distinct nonzero global ids ascending; off[n_ids+1]: CSR offsets;

@@ -86,6 +86,7 @@ SIGNATURES = {
     "sem_rhs": (_I, [_P, _P, _P, _P]),
     "sem_mass_local": (_I, [_P, _P, _P, _P]),
     "sem_dot": (_I, [_P, _P, _P, _P, _P]),
+    "sem_dot_static": (_I, [_P, _P, _P, C.c_int64, _P, _P]),
     "sem_get_maps": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "sem_get_geom": (_I, [_P, _I, _P]),
     "sem_get_geom_lowp": (_I, [_P, _I, _I, _P]),
