@@ -246,6 +246,37 @@ def solve_bench(ctx_cls, args, dev):
     return out
 
 
+def sweep_orders(ctx_cls, dev, stream, steps=100):
+    """Ax+gs throughput across orders at about 16.8M local points (nearest cube of elements)."""
+    import torch
+
+    import sem_inputs as si
+
+    out = []
+    for N in (3, 5, 7, 9, 11):
+        e1 = si.cube_for_points(N)
+        mesh = si.box_mesh(e1, N, warp=0.1, perm_seed=0)
+        ctx = ctx_cls.from_mesh(mesh, prec_copies=4, mg_orders=[N])
+        lv = ctx.levels[0]
+        u = torch.tensor(si.uniform_field(mesh, 0).ravel(), device=dev)
+        w = torch.empty_like(u)
+        row = {"N": N, "E": lv["E"], "n_L": lv["nL"], "n_G": lv["nG"]}
+        for name, pairs in (("fp64", False), ("fp32_pairs", True)):
+            fn = lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=True, pairs=pairs)
+            for _ in range(3):
+                fn()
+            t = time_events(fn, steps, stream)
+            ta = time_events(lambda: ctx.ax(u, w, h1=1.0, h2=0.5, assemble=False, pairs=pairs), steps, stream)
+            row[name] = {"gdofs": lv["nG"] * steps / t / 1e9, "ms_per_step": 1e3 * t / steps,
+                         "ax_ms": 1e3 * ta / steps,
+                         "ax_tflops_paper_count": ax_flops_per_element(N) * lv["E"] / (ta / steps) / 1e12}
+        out.append(row)
+        ctx.close()
+        del u, w
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,6 +293,8 @@ def main():
     ap.add_argument("--ax", default="fp64", choices=["fp64", "pairs"],
                     help="element kernel of the timed step: FP64 instructions or FP32-pair arithmetic")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also measure Ax+gs for N in 3,5,7,9,11 at about 16.8M local points")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -363,6 +396,8 @@ def main():
             "ax_kernel_ms": 1e3 * tva / args.steps, "dtype": "f32x2" if other else "f64",
             "ax_kernel_tflops_paper_count": flops / (tva / args.steps) / 1e12}}
     ctx.close()
+    if args.sweep:
+        line["sweep"] = sweep_orders(SemContext, dev, stream)
     if not args.no_solve:
         line["solve"] = solve_bench(SemContext, args, dev)
     if rank == 0 and not args.no_cpu and world == 1:

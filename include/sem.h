@@ -101,7 +101,7 @@ typedef struct {
   double cheb_lmax_factor;   /* (1.1) */
   int32_t lanczos_steps;     /* Lanczos steps for the eigenvalue estimate of D^-1 A (10) */
   uint64_t lanczos_seed;     /* SplitMix64 seed of the Lanczos start vector (1) */
-  double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-4) */
+  double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-2) */
   int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
   int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
 } sem_opts;

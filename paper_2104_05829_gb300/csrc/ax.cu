@@ -144,8 +144,7 @@ int launch_ax(const Level& L, const T* u, T* w, const GT* G, const typename MatT
 template <int NP>
 int ax_dispatch_np(const Level& L, int prec, const void* u, void* w, double h1, double h2, const double* h1L,
                    const double* skip, cudaStream_t s) {
-  if (prec == SEM_FP64)
-    return launch_ax<double, double, NP>(L, (const double*)u, (double*)w, L.G, L.D, h1, h2, h1L, skip, s);
+  if (prec == SEM_FP64) return ax_eo_apply(L, (const double*)u, (double*)w, h1, h2, h1L, skip, s);
   if (prec == SEM_FP32)
     return launch_ax<float, float, NP>(L, (const float*)u, (float*)w, L.G32, L.Df, h1, h2, h1L, skip, s);
   return launch_ax<float, __nv_bfloat16, NP>(L, (const float*)u, (float*)w, L.G16, L.Df, h1, h2, h1L, skip, s);

@@ -133,6 +133,8 @@ struct Ctx {
   int pc_prec = SEM_FP64;
   double pc_h1 = 0, pc_h2 = 0;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t cev[2] = {nullptr, nullptr};   // coarse-solve batch markers
+  double* h_done = nullptr;                  // pinned, 2 slots
 };
 
 constexpr int RED_BLOCKS = 304;   // 2 per SM on a 152-SM GB300; fixed for determinism
@@ -144,6 +146,10 @@ int ax_apply(const Level& L, int prec, const void* u, void* w, double h1, double
 int diag_local(const Level& L, double h1, double h2, const double* h1L, double* d, cudaStream_t s);
 int grad_h1_apply(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
 int geom_compute(Level& L, int* d_bad, cudaStream_t s);
+
+// ---- ax_eo.cu (FP64 element operator, even-odd contractions)
+int ax_eo_apply(const Level& L, const double* u, double* w, double h1, double h2, const double* h1L,
+                const double* skip, cudaStream_t s);
 
 // ---- ax_pairs.cu
 int pairs_build(Level& L, cudaStream_t s);

@@ -343,7 +343,7 @@ void sem_default_opts(sem_opts* o) {
   o->cheb_lmax_factor = 1.1;
   o->lanczos_steps = 10;
   o->lanczos_seed = 1;
-  o->coarse_tol = 1e-4;
+  o->coarse_tol = 1e-2;
   o->coarse_maxit = 100;
   o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
 }
@@ -372,6 +372,9 @@ void sem_free(sem_ctx* h) {
     if (p) cudaFree(p);
   if (C->h_scal) cudaFreeHost(C->h_scal);
   if (C->ev) cudaEventDestroy(C->ev);
+  for (auto& e : C->cev)
+    if (e) cudaEventDestroy(e);
+  if (C->h_done) cudaFreeHost(C->h_done);
   delete C;
 }
 
@@ -487,6 +490,9 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   STEP(dmalloc(&C->dr, nL));
   STEP(dmalloc(&C->t, nL));
   CUSTEP(cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming));
+  CUSTEP(cudaEventCreateWithFlags(&C->cev[0], cudaEventDisableTiming));
+  CUSTEP(cudaEventCreateWithFlags(&C->cev[1], cudaEventDisableTiming));
+  CUSTEP(cudaMallocHost((void**)&C->h_done, 2 * sizeof(double)));
   CUSTEP(cudaStreamSynchronize(s));
   cudaStreamDestroy(s);
 #undef STEP

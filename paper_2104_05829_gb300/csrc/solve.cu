@@ -212,11 +212,31 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   VecSet v = vecs(L, prec);
   double* sc = C.scal + 1 * S_NSLOTS;
   SEM_TRY(pcg_begin_tol(C, L, prec, b, nullptr, x, v.r, v.dinv, v.p, sc, C.opts.coarse_tol, s));
-  for (int it = 0; it < C.opts.coarse_maxit; ++it) {
-    SEM_TRY(level_op(C, l, prec, v.p, v.w, C.pc_h1, C.pc_h2, s, sc + S_DONE));
-    SEM_TRY(kr_alpha(C, L, prec, v.p, v.w, sc, s));
-    SEM_TRY(kr_update_jacobi(C, L, prec, x, v.p, v.r, v.w, v.dinv, sc, s));
-    SEM_TRY(kr_direction_jacobi(L, prec, v.p, v.r, v.dinv, sc, s));
+  // Iterations go out in batches. After each batch the device's "done" flag is
+  // copied to pinned host memory; the host looks at the previous batch's flag
+  // while the current batch runs, and stops launching once it is set. Launches
+  // that follow convergence return at once, so the result does not depend on
+  // where the host stops.
+  constexpr int BATCH = 6;
+  int launched = 0, q = 0;
+  bool pending = false;
+  while (launched < C.opts.coarse_maxit) {
+    const int nb = std::min(BATCH, C.opts.coarse_maxit - launched);
+    for (int it = 0; it < nb; ++it) {
+      SEM_TRY(level_op(C, l, prec, v.p, v.w, C.pc_h1, C.pc_h2, s, sc + S_DONE));
+      SEM_TRY(kr_alpha(C, L, prec, v.p, v.w, sc, s));
+      SEM_TRY(kr_update_jacobi(C, L, prec, x, v.p, v.r, v.w, v.dinv, sc, s));
+      SEM_TRY(kr_direction_jacobi(L, prec, v.p, v.r, v.dinv, sc, s));
+    }
+    launched += nb;
+    SEM_CUDA_TRY(cudaMemcpyAsync(C.h_done + q, sc + S_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA_TRY(cudaEventRecord(C.cev[q], s));
+    if (pending) {
+      SEM_CUDA_TRY(cudaEventSynchronize(C.cev[1 - q]));
+      if (C.h_done[1 - q] != 0.0) break;
+    }
+    pending = true;
+    q = 1 - q;
   }
   return SEM_OK;
 }
