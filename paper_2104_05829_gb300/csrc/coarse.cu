@@ -1,0 +1,328 @@
+// Coarsest-level Jacobi-PCG in one launch on one thread-block cluster.
+//
+// The coarse problem of the p-multigrid V-cycle (order 1 by default, a few
+// hundred thousand local points) is too small to fill the GPU, and a kernel
+// per Krylov step makes its iterations launch- and latency-bound. Here the
+// whole solve is one kernel on a single cluster of up to 16 CTAs:
+//  - phases (element operator, gather-scatter, vector updates) are separated
+//    by the hardware cluster barrier (barrier.cluster arrive/wait);
+//  - every dot product is reduced block-wise, the block partials are
+//    published in shared memory and every CTA reads all of them through
+//    distributed shared memory and adds them in rank order, so all CTAs hold
+//    the same bits and take the same branch (convergence, breakdown);
+//  - vectors live in global memory (they fit in L2).
+// The algorithm is the multi-kernel one: x0 = 0, r = b, z = D^-1 r, stop when
+// (r,r) <= tol^2 (b,b) or after maxit iterations. It serves the FP32 and
+// BF16-factor V-cycles at order 1 (one element per thread fits in registers);
+// per-thread sums are FP32, block and cluster sums FP64. The FP64 V-cycle keeps
+// the multi-kernel solve, which spreads its FP64 work over every SM.
+// w is written by one CTA (element operator, gather-scatter) and read by
+// others, so its accesses bypass L1 (__ldcg/__stcg); each CTA's point range is
+// exactly the points of its elements, so x, r, p stay CTA-local.
+#include <cooperative_groups.h>
+
+#include "sem_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sem {
+
+namespace {
+
+constexpr int CT = 1024;   // threads per CTA
+constexpr int NP = 2;      // order 1
+constexpr int NP3 = NP * NP * NP;
+
+struct CoarseArgs {
+  int E;
+  int64_t nseg;
+  const void* G;          // factors [E][7][8] (FP32 or BF16)
+  const float* b;
+  float* x;
+  float* r;
+  float* p;
+  float* w;
+  const float* dinv;
+  const uint8_t* own;
+  const int32_t* seg_off;
+  const int32_t* seg_idx;
+  const uint8_t* seg_dir;
+  float h1, h2;
+  double tol;
+  int maxit;
+  double* sc;             // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
+};
+
+__device__ __forceinline__ float gload(const float* G, int64_t q) { return G[q]; }
+__device__ __forceinline__ float gload(const __nv_bfloat16* G, int64_t q) { return __bfloat162float(G[q]); }
+
+// Sum of `v` over the cluster, identical in every CTA: warp and block trees,
+// then the block partials in rank order through distributed shared memory.
+// The two slot buffers alternate, so one cluster barrier per sum suffices: a
+// slot is rewritten only after the next sum's barrier, which every CTA reaches
+// after it has read the slot.
+template <int NS>
+__device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity, cg::cluster_group& cl) {
+  __shared__ double s_w[CT / 32][NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_xor_sync(0xffffffffu, v[s], o);
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int q = 0; q < CT / 32; ++q) t += s_w[q][s];
+      (*slots)[parity][s] = t;
+    }
+  }
+  cl.sync();
+  const unsigned ncta = cl.num_blocks();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double t = 0;
+    for (unsigned q = 0; q < ncta; ++q) {
+      double(*rs)[2][4] = cl.map_shared_rank(slots, q);
+      t += (*rs)[parity][s];
+    }
+    v[s] = t;
+  }
+  parity ^= 1;
+  __syncthreads();   // s_w is reused by the next sum
+}
+
+// w = A_L p for the elements [e0, e1), one element per thread.
+template <typename GT>
+__device__ void element_ax(const CoarseArgs& a, const Mat32& D, int e0, int e1) {
+  constexpr int NP2 = NP * NP;
+  const GT* G = static_cast<const GT*>(a.G);
+  for (int e = e0 + threadIdx.x; e < e1; e += CT) {
+    const int64_t base = (int64_t)e * NP3;
+    float u[NP3], wr[NP3], ws[NP3], wt[NP3];
+#pragma unroll
+    for (int q = 0; q < NP3; ++q) u[q] = a.p[base + q];
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          float ur = 0.f, us = 0.f, ut = 0.f;
+#pragma unroll
+          for (int l = 0; l < NP; ++l) {
+            ur = fmaf(D.a[i * NP + l], u[k * NP2 + j * NP + l], ur);
+            us = fmaf(D.a[j * NP + l], u[k * NP2 + l * NP + i], us);
+            ut = fmaf(D.a[k * NP + l], u[l * NP2 + j * NP + i], ut);
+          }
+          const int q = k * NP2 + j * NP + i;
+          const int64_t gb = (int64_t)e * 7 * NP3 + q;
+          const float g11 = gload(G, gb), g12 = gload(G, gb + NP3), g13 = gload(G, gb + 2 * NP3);
+          const float g22 = gload(G, gb + 3 * NP3), g23 = gload(G, gb + 4 * NP3), g33 = gload(G, gb + 5 * NP3);
+          wr[q] = a.h1 * (g11 * ur + g12 * us + g13 * ut);
+          ws[q] = a.h1 * (g12 * ur + g22 * us + g23 * ut);
+          wt[q] = a.h1 * (g13 * ur + g23 * us + g33 * ut);
+        }
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+#pragma unroll
+      for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const int q = k * NP2 + j * NP + i;
+          float acc = a.h2 * gload(G, (int64_t)e * 7 * NP3 + 6 * NP3 + q) * u[q];
+#pragma unroll
+          for (int l = 0; l < NP; ++l) {
+            acc = fmaf(D.a[l * NP + i], wr[k * NP2 + j * NP + l], acc);
+            acc = fmaf(D.a[l * NP + j], ws[k * NP2 + l * NP + i], acc);
+            acc = fmaf(D.a[l * NP + k], wt[l * NP2 + j * NP + i], acc);
+          }
+          __stcg(a.w + base + q, acc);
+        }
+  }
+}
+
+template <typename GT>
+__global__ void __launch_bounds__(CT) k_coarse_pcg(CoarseArgs a, Mat32 D) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double slots[2][4];
+  int parity = 0;
+  const unsigned rank = cl.block_rank(), ncta = cl.num_blocks();
+  const int e0 = (int)((int64_t)a.E * rank / ncta), e1 = (int)((int64_t)a.E * (rank + 1) / ncta);
+  const int64_t p0 = (int64_t)e0 * NP3, p1 = (int64_t)e1 * NP3;
+  const int64_t s0 = a.nseg * rank / ncta, s1 = a.nseg * (rank + 1) / ncta;
+
+  // start: x = 0, r = b, p = D^-1 r; (b,b), (r,z), (r,r)
+  float f0 = 0.f, f1 = 0.f;
+  for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) {
+    const float bl = a.b[l];
+    a.x[l] = 0.f;
+    a.r[l] = bl;
+    const float zl = a.dinv[l] * bl;
+    a.p[l] = zl;
+    if (a.own[l]) {
+      f0 = fmaf(bl, bl, f0);
+      f1 = fmaf(bl, zl, f1);
+    }
+  }
+  double v3[3] = {f0, f1, f0};
+  cluster_sum<3>(v3, &slots, parity, cl);
+  const double bb = v3[0];
+  double rz = v3[1], rr = v3[2];
+  const double tol2 = a.tol * a.tol * bb;
+  int it = 0, brk = 0;
+  bool done = rr <= tol2;
+  while (!done && it < a.maxit) {
+    cl.sync();   // p complete in every CTA
+    element_ax<GT>(a, D, e0, e1);
+    cl.sync();   // w complete before the gather-scatter reads other CTAs' copies
+    for (int64_t sg = s0 + threadIdx.x; sg < s1; sg += CT) {
+      const int bgn = a.seg_off[sg], end = a.seg_off[sg + 1];
+      if (a.seg_dir[sg]) {
+        for (int q = bgn; q < end; ++q) __stcg(a.w + a.seg_idx[q], 0.f);
+      } else if (end - bgn > 1) {
+        float sum = __ldcg(a.w + a.seg_idx[bgn]);
+        for (int q = bgn + 1; q < end; ++q) sum += __ldcg(a.w + a.seg_idx[q]);
+        for (int q = bgn; q < end; ++q) __stcg(a.w + a.seg_idx[q], sum);
+      }
+    }
+    cl.sync();   // assembled w visible
+    float g = 0.f;
+    for (int64_t l = p0 + threadIdx.x; l < p1; l += CT)
+      if (a.own[l]) g = fmaf(a.p[l], __ldcg(a.w + l), g);
+    double v1[1] = {g};
+    cluster_sum<1>(v1, &slots, parity, cl);
+    const double pw = v1[0];
+    if (!(pw > 0.0) || !isfinite(pw)) {
+      brk = 1;
+      break;
+    }
+    const float at = (float)(rz / pw);
+    float q0 = 0.f, q1 = 0.f;
+    for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) {
+      a.x[l] = fmaf(at, a.p[l], a.x[l]);
+      const float rl = fmaf(-at, __ldcg(a.w + l), a.r[l]);
+      a.r[l] = rl;
+      if (a.own[l]) {
+        q0 = fmaf(rl, rl, q0);
+        q1 = fmaf(rl, a.dinv[l] * rl, q1);
+      }
+    }
+    double v2[2] = {q0, q1};
+    cluster_sum<2>(v2, &slots, parity, cl);
+    ++it;
+    rr = v2[0];
+    const double beta = v2[1] / rz;
+    rz = v2[1];
+    if (!isfinite(rr)) {
+      brk = 1;
+      break;
+    }
+    if (rr <= tol2) break;
+    const float bt = (float)beta;
+    for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) a.p[l] = fmaf(bt, a.p[l], a.dinv[l] * a.r[l]);
+  }
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    a.sc[S_ITER] = it;
+    a.sc[S_TOTAL] += it;
+    a.sc[S_RR] = rr;
+    a.sc[S_BB] = bb;
+    a.sc[S_BREAK] = brk;
+    a.sc[S_DONE] = 1;
+  }
+}
+
+cudaLaunchConfig_t cluster_cfg(int cl, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(CT);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Largest cluster (16, 8, 4, 2 CTAs) the device can schedule for this kernel.
+template <typename GT>
+int cluster_size(cudaStream_t s) {
+  static int cached[2] = {-1, -1};
+  int& c = cached[sizeof(GT) == 4 ? 0 : 1];
+  if (c >= 0) return c;
+  const void* f = (const void*)k_coarse_pcg<GT>;
+  c = 0;
+  for (int cl : {16, 8, 4, 2}) {
+    if (cl > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_cfg(cl, s, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, f, &cfg) == cudaSuccess && n >= 1) {
+      c = cl;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return c;
+}
+
+template <typename GT>
+int launch_coarse(const Level& L, const GT* G, const float* b, float* x, float* r, float* p, float* w,
+                  const float* dinv, double h1, double h2, double tol, int maxit, double* sc, cudaStream_t s,
+                  bool* used) {
+  *used = false;
+  const int cl = cluster_size<GT>(s);
+  if (cl == 0) return SEM_OK;
+  CoarseArgs a{};
+  a.E = L.E;
+  a.nseg = L.n_seg;
+  a.G = G;
+  a.b = b;
+  a.x = x;
+  a.r = r;
+  a.p = p;
+  a.w = w;
+  a.dinv = dinv;
+  a.own = L.owner;
+  a.seg_off = L.seg_off;
+  a.seg_idx = L.seg_idx;
+  a.seg_dir = L.seg_dir;
+  a.h1 = (float)h1;
+  a.h2 = (float)h2;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.sc = sc;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_cfg(cl, s, attr);
+  SEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_pcg<GT>, a, L.Df));
+  *used = true;
+  return SEM_OK;
+}
+
+}  // namespace
+
+// One-launch coarse solve for the FP32 / BF16-factor V-cycle at order 1;
+// *used = false when it does not apply (FP64, another order, no cluster fits).
+int coarse_cluster_solve(const Level& L, int prec, const void* b, void* x, void* r, void* p, void* w,
+                         const void* dinv, double h1, double h2, double tol, int maxit, double* sc,
+                         cudaStream_t s, bool* used) {
+  *used = false;
+  if (L.NP != NP || prec == SEM_FP64) return SEM_OK;
+  if (prec == SEM_FP32)
+    return launch_coarse<float>(L, L.G32, (const float*)b, (float*)x, (float*)r, (float*)p, (float*)w,
+                                (const float*)dinv, h1, h2, tol, maxit, sc, s, used);
+  return launch_coarse<__nv_bfloat16>(L, L.G16, (const float*)b, (float*)x, (float*)r, (float*)p, (float*)w,
+                                      (const float*)dinv, h1, h2, tol, maxit, sc, s, used);
+}
+
+}  // namespace sem

@@ -155,6 +155,11 @@ int ax_eo_apply(const Level& L, const double* u, double* w, double h1, double h2
 int pairs_build(Level& L, cudaStream_t s);
 int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s);
 
+// ---- coarse.cu: one-launch coarse Jacobi-PCG on a thread-block cluster
+int coarse_cluster_solve(const Level& L, int prec, const void* b, void* x, void* r, void* p, void* w,
+                         const void* dinv, double h1, double h2, double tol, int maxit, double* sc,
+                         cudaStream_t s, bool* used);
+
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);
 int gs_apply_skip(const Level& L, int prec, void* w, bool mask, const double* skip, cudaStream_t s);

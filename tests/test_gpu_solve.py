@@ -178,3 +178,22 @@ def test_pmg_solve_with_pair_arithmetic_outer_operator():
     xg = global_from_L(lev, H(x))
     true_res = np.linalg.norm(bg - lev.apply(xg)) / np.linalg.norm(bg)
     assert info["relres"] <= 1e-8 and true_res < 2e-8
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16g", 5e-2)])
+def test_low_precision_vcycle_matches_oracle(prec, tol):
+    """FP32 / BF16-factor V-cycle (order-1 coarse solve in one cluster launch) against
+    the FP64 oracle V-cycle with the same eigenvalue bounds and 8 coarse iterations.
+    Tolerance: FP32 rounding (6e-8) amplified by the V-cycle's operator norm, and the
+    BF16 factor rounding (4e-3) for the BF16 variant."""
+    dev()
+    mesh, ctx, levels = _mg_pair(shape=(4, 3, 3), N=7, orders=(7, 3, 1))
+    ctx.precond_setup(1.0, 0.0, prec)
+    params = O.MGParams(coarse_tol=0.0, coarse_maxit=8, lmax=ctx.lmax())
+    mg = O.PMG(levels, params=params)
+    L0 = levels[0]
+    r = L0.mask(np.random.default_rng(5).standard_normal(L0.n_G))
+    z = H(ctx.vcycle(T(_gL(L0, r))))
+    err = relmax(z, _gL(L0, mg(r)))
+    print(f"{prec} V-cycle relmax {err:.3e}")
+    assert err < tol
