@@ -45,6 +45,29 @@ def ax_gs_bytes(nL: int, n_shared: int, nG: int, helmholtz: bool = True) -> int:
     return (56 if helmholtz else 48) * nL + 4 * n_shared + 16 * nG
 
 
+def kernel_source_hash() -> str:
+    """SHA-256 of the element-kernel source, to tell whether recorded ncu counters are current."""
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2104_05829_gb300", "csrc", "ax_eo.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, elements: int):
+    """DRAM bytes per launch of `kernel` from the ncu capture recorded in profiles/traffic.json,
+    scaled to `elements` (traffic grows in proportion to the elements processed); None when no
+    capture exists or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes"] * elements / rec["elements"]
+
+
 def peaks():
     p = {"hbm_gbs": 6686.5, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -216,6 +239,9 @@ def solve_bench(ctx_cls, args, dev):
     stream = torch.cuda.current_stream()
     variants = (("fp64", "fp64", False), ("fp32", "fp32", False), ("bf16g", "bf16g", False),
                 ("fp32_outer_pairs", "fp32", True))
+    if args.solve_variants:
+        keep = set(args.solve_variants.split(","))
+        variants = tuple(v for v in variants if v[0] in keep)
     for name, prec, op in variants:
         solve = lambda: ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled", outer_pairs=op)
         solve()   # warm-up, includes the preconditioner setup for this precision
@@ -286,6 +312,7 @@ def main():
     ap.add_argument("--elements", type=int, default=32, help="elements per side of the Ax box")
     ap.add_argument("--solve-elements", type=int, default=24)
     ap.add_argument("--solve-reps", type=int, default=3)
+    ap.add_argument("--solve-variants", default="", help="comma list of fp64,fp32,bf16g,fp32_outer_pairs")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -349,9 +376,10 @@ def main():
     t_ax_launch = t_ax / args.steps
     achieved_tf = flops / t_ax_launch / 1e12
     bytes_alg = ax_gs_bytes(nL, n_shared, nG)
+    kname = "k_ax_eo<ArPair,8>" if pairs else "k_ax_eo<ArF64,8>"
     roof = {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-            "frac": achieved_tf / pk["fp64_tflops"], "traffic": None,
-            "kernel": "k_ax_pairs<8> (FP32-pair local Ax)" if pairs else "k_ax<double,double,8> (FP64 local Ax)",
+            "frac": achieved_tf / pk["fp64_tflops"], "traffic": recorded_traffic(kname, E),
+            "kernel": kname + (" (FP32-pair local Ax)" if pairs else " (FP64 local Ax, even-odd)"),
             "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
             "hbm_view": {"bytes_per_step": bytes_alg, "achieved_gbs": bytes_alg / (ms / 1e3) / 1e9,
                          "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],

@@ -7,9 +7,9 @@
 //  - phases (element operator, gather-scatter, vector updates) are separated
 //    by the hardware cluster barrier (barrier.cluster arrive/wait);
 //  - every dot product is reduced block-wise, the block partials are
-//    published in shared memory and every CTA reads all of them through
-//    distributed shared memory and adds them in rank order, so all CTAs hold
-//    the same bits and take the same branch (convergence, breakdown);
+//    published in shared memory and one warp of every CTA reads all of them
+//    through distributed shared memory and adds them in a fixed order, so all
+//    CTAs hold the same bits and take the same branch (convergence, breakdown);
 //  - vectors live in global memory (they fit in L2).
 // The algorithm is the multi-kernel one: x0 = 0, r = b, z = D^-1 r, stop when
 // (r,r) <= tol^2 (b,b) or after maxit iterations. It serves the FP32 and
@@ -57,13 +57,15 @@ __device__ __forceinline__ float gload(const float* G, int64_t q) { return G[q];
 __device__ __forceinline__ float gload(const __nv_bfloat16* G, int64_t q) { return __bfloat162float(G[q]); }
 
 // Sum of `v` over the cluster, identical in every CTA: warp and block trees,
-// then the block partials in rank order through distributed shared memory.
-// The two slot buffers alternate, so one cluster barrier per sum suffices: a
-// slot is rewritten only after the next sum's barrier, which every CTA reaches
-// after it has read the slot.
+// then warp 0 fetches the block partials of all CTAs through distributed
+// shared memory (lane q reads CTA q) and adds them in a fixed shuffle tree;
+// the total is broadcast through shared memory. The two slot buffers
+// alternate, so one cluster barrier per sum suffices: a slot is rewritten only
+// after the next sum's barrier, which every CTA reaches after reading it.
 template <int NS>
 __device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity, cg::cluster_group& cl) {
   __shared__ double s_w[CT / 32][NS];
+  __shared__ double s_tot[NS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -73,27 +75,35 @@ __device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity,
 #pragma unroll
     for (int s = 0; s < NS; ++s) s_w[warp][s] = v[s];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      double t = 0;
-      for (int q = 0; q < CT / 32; ++q) t += s_w[q][s];
-      (*slots)[parity][s] = t;
+      double t = s_w[lane][s];   // CT / 32 == 32 warps: one partial per lane
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) (*slots)[parity][s] = t;
     }
   }
   cl.sync();
-  const unsigned ncta = cl.num_blocks();
+  if (warp == 0) {
+    const unsigned ncta = cl.num_blocks();
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    double t = 0;
-    for (unsigned q = 0; q < ncta; ++q) {
-      double(*rs)[2][4] = cl.map_shared_rank(slots, q);
-      t += (*rs)[parity][s];
+    for (int s = 0; s < NS; ++s) {
+      double t = 0.0;
+      if ((unsigned)lane < ncta) {
+        double(*rs)[2][4] = cl.map_shared_rank(slots, (unsigned)lane);
+        t = (*rs)[parity][s];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) s_tot[s] = t;
     }
-    v[s] = t;
   }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NS; ++s) v[s] = s_tot[s];
   parity ^= 1;
-  __syncthreads();   // s_w is reused by the next sum
+  __syncthreads();   // s_w and s_tot are reused by the next sum
 }
 
 // w = A_L p for the elements [e0, e1), one element per thread.

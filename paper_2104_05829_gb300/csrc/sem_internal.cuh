@@ -151,7 +151,7 @@ int geom_compute(Level& L, int* d_bad, cudaStream_t s);
 int ax_eo_apply(const Level& L, const double* u, double* w, double h1, double h2, const double* h1L,
                 const double* skip, cudaStream_t s);
 
-// ---- ax_pairs.cu
+// ---- ax_eo.cu (FP32-pair variant)
 int pairs_build(Level& L, cudaStream_t s);
 int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s);
 
