@@ -106,58 +106,47 @@ __device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity,
   __syncthreads();   // s_w and s_tot are reused by the next sum
 }
 
-// w = A_L p for the elements [e0, e1), one element per thread.
+// w = A_L p for the points [p0, p1) (whole elements), one point per thread.
+// At order 1 the 8 points of an element are 8 consecutive lanes of a warp and
+// the neighbour of point (i, j, k) along r, s, t is the lane with bit 0, 1 or
+// 2 flipped, so every contraction is one shuffle: (D v)_a = D[a][a] v_a + D[a][1-a] v_partner.
 template <typename GT>
-__device__ void element_ax(const CoarseArgs& a, const Mat32& D, int e0, int e1) {
-  constexpr int NP2 = NP * NP;
+__device__ void element_ax(const CoarseArgs& a, const Mat32& D, int64_t p0, int64_t p1) {
   const GT* G = static_cast<const GT*>(a.G);
-  for (int e = e0 + threadIdx.x; e < e1; e += CT) {
-    const int64_t base = (int64_t)e * NP3;
-    float u[NP3], wr[NP3], ws[NP3], wt[NP3];
-#pragma unroll
-    for (int q = 0; q < NP3; ++q) u[q] = a.p[base + q];
-#pragma unroll
-    for (int k = 0; k < NP; ++k)
-#pragma unroll
-      for (int j = 0; j < NP; ++j)
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          float ur = 0.f, us = 0.f, ut = 0.f;
-#pragma unroll
-          for (int l = 0; l < NP; ++l) {
-            ur = fmaf(D.a[i * NP + l], u[k * NP2 + j * NP + l], ur);
-            us = fmaf(D.a[j * NP + l], u[k * NP2 + l * NP + i], us);
-            ut = fmaf(D.a[k * NP + l], u[l * NP2 + j * NP + i], ut);
-          }
-          const int q = k * NP2 + j * NP + i;
-          const int64_t gb = (int64_t)e * 7 * NP3 + q;
-          const float g11 = gload(G, gb), g12 = gload(G, gb + NP3), g13 = gload(G, gb + 2 * NP3);
-          const float g22 = gload(G, gb + 3 * NP3), g23 = gload(G, gb + 4 * NP3), g33 = gload(G, gb + 5 * NP3);
-          wr[q] = a.h1 * (g11 * ur + g12 * us + g13 * ut);
-          ws[q] = a.h1 * (g12 * ur + g22 * us + g23 * ut);
-          wt[q] = a.h1 * (g13 * ur + g23 * us + g33 * ut);
-        }
-#pragma unroll
-    for (int k = 0; k < NP; ++k)
-#pragma unroll
-      for (int j = 0; j < NP; ++j)
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          const int q = k * NP2 + j * NP + i;
-          float acc = a.h2 * gload(G, (int64_t)e * 7 * NP3 + 6 * NP3 + q) * u[q];
-#pragma unroll
-          for (int l = 0; l < NP; ++l) {
-            acc = fmaf(D.a[l * NP + i], wr[k * NP2 + j * NP + l], acc);
-            acc = fmaf(D.a[l * NP + j], ws[k * NP2 + l * NP + i], acc);
-            acc = fmaf(D.a[l * NP + k], wt[l * NP2 + j * NP + i], acc);
-          }
-          __stcg(a.w + base + q, acc);
-        }
+  const int q = threadIdx.x & 7;                 // point within the element
+  const int i = q & 1, j = (q >> 1) & 1, k = q >> 2;
+  const float d00 = D.a[0], d01 = D.a[1], d10 = D.a[2], d11 = D.a[3];
+  const float di_s = i ? d11 : d00, di_o = i ? d10 : d01;   // D[i][i], D[i][1-i]
+  const float dj_s = j ? d11 : d00, dj_o = j ? d10 : d01;
+  const float dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
+  const float ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;   // D[1-a][a]
+  // CT is a multiple of 8, and p0, p1 are multiples of 8: every warp pass covers whole elements
+  for (int64_t l = p0 + threadIdx.x; l < p1 + ((p1 - p0) % CT ? CT - (p1 - p0) % CT : 0); l += CT) {
+    const bool live = l < p1;
+    const float u = live ? a.p[l] : 0.f;
+    const float ur = di_s * u + di_o * __shfl_xor_sync(0xffffffffu, u, 1);
+    const float us = dj_s * u + dj_o * __shfl_xor_sync(0xffffffffu, u, 2);
+    const float ut = dk_s * u + dk_o * __shfl_xor_sync(0xffffffffu, u, 4);
+    float wr = 0.f, ws = 0.f, wt = 0.f, bu = 0.f;
+    if (live) {
+      const int64_t e = l >> 3;
+      const int64_t gb = e * 7 * NP3 + q;
+      const float g11 = gload(G, gb), g12 = gload(G, gb + NP3), g13 = gload(G, gb + 2 * NP3);
+      const float g22 = gload(G, gb + 3 * NP3), g23 = gload(G, gb + 4 * NP3), g33 = gload(G, gb + 5 * NP3);
+      wr = a.h1 * (g11 * ur + g12 * us + g13 * ut);
+      ws = a.h1 * (g12 * ur + g22 * us + g23 * ut);
+      wt = a.h1 * (g13 * ur + g23 * us + g33 * ut);
+      bu = a.h2 * gload(G, gb + 6 * NP3) * u;
+    }
+    float acc = bu + di_s * wr + ti_o * __shfl_xor_sync(0xffffffffu, wr, 1);
+    acc += dj_s * ws + tj_o * __shfl_xor_sync(0xffffffffu, ws, 2);
+    acc += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
+    if (live) __stcg(a.w + l, acc);
   }
 }
 
 template <typename GT>
-__global__ void __launch_bounds__(CT) k_coarse_pcg(CoarseArgs a, Mat32 D) {
+__global__ void __maxnreg__(64) k_coarse_pcg(CoarseArgs a, Mat32 D) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double slots[2][4];
   int parity = 0;
@@ -188,7 +177,7 @@ __global__ void __launch_bounds__(CT) k_coarse_pcg(CoarseArgs a, Mat32 D) {
   bool done = rr <= tol2;
   while (!done && it < a.maxit) {
     cl.sync();   // p complete in every CTA
-    element_ax<GT>(a, D, e0, e1);
+    element_ax<GT>(a, D, p0, p1);
     cl.sync();   // w complete before the gather-scatter reads other CTAs' copies
     for (int64_t sg = s0 + threadIdx.x; sg < s1; sg += CT) {
       const int bgn = a.seg_off[sg], end = a.seg_off[sg + 1];
