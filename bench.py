@@ -45,13 +45,18 @@ def ax_gs_bytes(nL: int, n_shared: int, nG: int, helmholtz: bool = True) -> int:
     return (56 if helmholtz else 48) * nL + 4 * n_shared + 16 * nG
 
 
-def kernel_source_hash() -> str:
-    """SHA-256 of the element-kernel source, to tell whether recorded ncu counters are current."""
+KERNEL_SOURCES = {"k_ax_eo<ArF64,8>": ["ax_eo.cu"], "k_ax_eo<ArPair,8>": ["ax_eo.cu", "pairs.cuh"]}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """SHA-256 over the sources a kernel is built from, to tell whether recorded ncu counters are current."""
     import hashlib
 
-    path = os.path.join(ROOT, "paper_2104_05829_gb300", "csrc", "ax_eo.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2104_05829_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, elements: int):
@@ -63,7 +68,7 @@ def recorded_traffic(kernel: str, elements: int):
         return None
     with open(path) as f:
         rec = json.load(f).get(kernel)
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(kernel):
         return None
     return rec["dram_bytes"] * elements / rec["elements"]
 
@@ -313,6 +318,7 @@ def main():
     ap.add_argument("--solve-elements", type=int, default=24)
     ap.add_argument("--solve-reps", type=int, default=3)
     ap.add_argument("--solve-variants", default="", help="comma list of fp64,fp32,bf16g,fp32_outer_pairs")
+    ap.add_argument("--solve-48", action="store_true", help="also time the 48^3-element (56.6M-point) solve")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -428,6 +434,11 @@ def main():
         line["sweep"] = sweep_orders(SemContext, dev, stream)
     if not args.no_solve:
         line["solve"] = solve_bench(SemContext, args, dev)
+    if args.solve_48:
+        import copy
+        a48 = copy.copy(args)
+        a48.solve_elements, a48.solve_reps = 48, 1
+        line["solve_48"] = solve_bench(SemContext, a48, dev)
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = oracle_ax_gs_rate(mesh)
     if rank == 0:

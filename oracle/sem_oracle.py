@@ -165,10 +165,16 @@ def geometry(x, y, z, N: int):
     G11, G12, G13, G22, G23, G33 of eq. gij, B = rho_ijk J_ijk (eq. vBu) and Jac
     the Jacobian determinant. The metric matrix dx_p/dr_q = D_q x_p is inverted
     pointwise by cofactors (eq. grad) to give dr_q/dx_p.
+
+    The coordinates are differentiated relative to each element's first node:
+    D_q (x_p - c) = D_q x_p because D_hat differentiates constants to zero
+    (eq. dh). In floating point the rows of D_hat sum to ~1e-15 rather than 0,
+    and on small elements far from the origin that rounding times the absolute
+    coordinate would dominate the metrics; the shift removes it.
     """
     xi, rho = gll(N)
     D = deriv_matrix(N)
-    d = [grad_ref(c, D) for c in (x, y, z)]  # d[p][q] = dx_p / dr_q
+    d = [grad_ref(c - c[:, :1, :1, :1], D) for c in (x, y, z)]  # d[p][q] = dx_p / dr_q
     a, b, c = d[0]
     dd, e, f = d[1]
     g, h, i = d[2]

@@ -165,13 +165,17 @@ __global__ void k_geom(int E, const double* __restrict__ x, const double* __rest
   const int loc = (int)(p - e * NP3);
   const int k = loc / NP2, j = (loc / NP) % NP, i = loc % NP;
   const double* X[3] = {x + e * NP3, y + e * NP3, z + e * NP3};
+  // coordinates relative to the element's first node: D_hat annihilates
+  // constants, and the shift keeps the rounding of D_hat's row sums (~1e-15)
+  // times a large absolute coordinate out of the metrics
   double M[3][3];
   for (int c = 0; c < 3; ++c) {
+    const double x0 = X[c][0];
     double dr = 0, ds = 0, dt = 0;
     for (int l = 0; l < NP; ++l) {
-      dr += Dm.a[i * NP + l] * X[c][k * NP2 + j * NP + l];
-      ds += Dm.a[j * NP + l] * X[c][k * NP2 + l * NP + i];
-      dt += Dm.a[k * NP + l] * X[c][l * NP2 + j * NP + i];
+      dr += Dm.a[i * NP + l] * (X[c][k * NP2 + j * NP + l] - x0);
+      ds += Dm.a[j * NP + l] * (X[c][k * NP2 + l * NP + i] - x0);
+      dt += Dm.a[k * NP + l] * (X[c][l * NP2 + j * NP + i] - x0);
     }
     M[c][0] = dr;
     M[c][1] = ds;

@@ -56,16 +56,17 @@ struct CoarseArgs {
 __device__ __forceinline__ float gload(const float* G, int64_t q) { return G[q]; }
 __device__ __forceinline__ float gload(const __nv_bfloat16* G, int64_t q) { return __bfloat162float(G[q]); }
 
-// Sum of `v` over the cluster, identical in every CTA: warp and block trees,
-// then warp 0 fetches the block partials of all CTAs through distributed
-// shared memory (lane q reads CTA q) and adds them in a fixed shuffle tree;
-// the total is broadcast through shared memory. The two slot buffers
-// alternate, so one cluster barrier per sum suffices: a slot is rewritten only
-// after the next sum's barrier, which every CTA reaches after reading it.
+// Cluster-wide sums of per-thread FP32 partials, identical in every CTA: FP32
+// warp trees, the 32 warp partials of the block in FP64 by warp 0, then warp 0
+// fetches the block partials of all CTAs through distributed shared memory
+// (lane q reads CTA q) and adds them in a fixed shuffle tree. The totals land in
+// `tot` (shared). The two slot buffers alternate, so one cluster barrier per sum
+// suffices: a slot is rewritten only after the next sum's barrier, which every
+// CTA reaches after reading it. FP64 work stays in one warp per CTA.
 template <int NS>
-__device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity, cg::cluster_group& cl) {
-  __shared__ double s_w[CT / 32][NS];
-  __shared__ double s_tot[NS];
+__device__ void cluster_sum(float (&v)[NS], double (*slots)[2][4], double* tot, int& parity,
+                            cg::cluster_group& cl) {
+  __shared__ float s_w[CT / 32][NS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -78,7 +79,7 @@ __device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity,
   if (warp == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      double t = s_w[lane][s];   // CT / 32 == 32 warps: one partial per lane
+      double t = (double)s_w[lane][s];   // CT / 32 == 32 warps: one partial per lane
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) (*slots)[parity][s] = t;
@@ -96,14 +97,11 @@ __device__ void cluster_sum(double (&v)[NS], double (*slots)[2][4], int& parity,
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) s_tot[s] = t;
+      if (lane == 0) tot[s] = t;
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < NS; ++s) v[s] = s_tot[s];
   parity ^= 1;
-  __syncthreads();   // s_w and s_tot are reused by the next sum
+  __syncthreads();   // tot visible; s_w free for the next sum
 }
 
 // w = A_L p for the points [p0, p1) (whole elements), one point per thread.
@@ -149,14 +147,20 @@ template <typename GT>
 __global__ void __maxnreg__(64) k_coarse_pcg(CoarseArgs a, Mat32 D) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double slots[2][4];
+  __shared__ double tot[4];
+  __shared__ float s_alpha, s_beta;
+  __shared__ int s_flag;   // 0 go on, 1 converged, 2 breakdown
   int parity = 0;
   const unsigned rank = cl.block_rank(), ncta = cl.num_blocks();
   const int e0 = (int)((int64_t)a.E * rank / ncta), e1 = (int)((int64_t)a.E * (rank + 1) / ncta);
   const int64_t p0 = (int64_t)e0 * NP3, p1 = (int64_t)e1 * NP3;
   const int64_t s0 = a.nseg * rank / ncta, s1 = a.nseg * (rank + 1) / ncta;
+  const bool lead = threadIdx.x == 0;
+  // scalars kept by the lead thread only (identical in every CTA)
+  double bb = 0, rz = 0, rr = 0, tol2 = 0;
 
-  // start: x = 0, r = b, p = D^-1 r; (b,b), (r,z), (r,r)
-  float f0 = 0.f, f1 = 0.f;
+  // start: x = 0, r = b, p = D^-1 r; (b,b), (r,z)
+  float f2[2] = {0.f, 0.f};
   for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) {
     const float bl = a.b[l];
     a.x[l] = 0.f;
@@ -164,18 +168,21 @@ __global__ void __maxnreg__(64) k_coarse_pcg(CoarseArgs a, Mat32 D) {
     const float zl = a.dinv[l] * bl;
     a.p[l] = zl;
     if (a.own[l]) {
-      f0 = fmaf(bl, bl, f0);
-      f1 = fmaf(bl, zl, f1);
+      f2[0] = fmaf(bl, bl, f2[0]);
+      f2[1] = fmaf(bl, zl, f2[1]);
     }
   }
-  double v3[3] = {f0, f1, f0};
-  cluster_sum<3>(v3, &slots, parity, cl);
-  const double bb = v3[0];
-  double rz = v3[1], rr = v3[2];
-  const double tol2 = a.tol * a.tol * bb;
-  int it = 0, brk = 0;
-  bool done = rr <= tol2;
-  while (!done && it < a.maxit) {
+  cluster_sum<2>(f2, &slots, tot, parity, cl);
+  if (lead) {
+    bb = tot[0];
+    rz = tot[1];
+    rr = bb;
+    tol2 = a.tol * a.tol * bb;
+    s_flag = rr <= tol2 ? 1 : 0;
+  }
+  __syncthreads();
+  int it = 0;
+  while (s_flag == 0 && it < a.maxit) {
     cl.sync();   // p complete in every CTA
     element_ax<GT>(a, D, p0, p1);
     cl.sync();   // w complete before the gather-scatter reads other CTAs' copies
@@ -190,48 +197,49 @@ __global__ void __maxnreg__(64) k_coarse_pcg(CoarseArgs a, Mat32 D) {
       }
     }
     cl.sync();   // assembled w visible
-    float g = 0.f;
+    float g[1] = {0.f};
     for (int64_t l = p0 + threadIdx.x; l < p1; l += CT)
-      if (a.own[l]) g = fmaf(a.p[l], __ldcg(a.w + l), g);
-    double v1[1] = {g};
-    cluster_sum<1>(v1, &slots, parity, cl);
-    const double pw = v1[0];
-    if (!(pw > 0.0) || !isfinite(pw)) {
-      brk = 1;
-      break;
+      if (a.own[l]) g[0] = fmaf(a.p[l], __ldcg(a.w + l), g[0]);
+    cluster_sum<1>(g, &slots, tot, parity, cl);
+    if (lead) {
+      const double pw = tot[0];
+      if (!(pw > 0.0) || !isfinite(pw)) s_flag = 2;
+      else s_alpha = (float)(rz / pw);
     }
-    const float at = (float)(rz / pw);
-    float q0 = 0.f, q1 = 0.f;
+    __syncthreads();
+    if (s_flag != 0) break;
+    const float at = s_alpha;
+    float q2[2] = {0.f, 0.f};
     for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) {
       a.x[l] = fmaf(at, a.p[l], a.x[l]);
       const float rl = fmaf(-at, __ldcg(a.w + l), a.r[l]);
       a.r[l] = rl;
       if (a.own[l]) {
-        q0 = fmaf(rl, rl, q0);
-        q1 = fmaf(rl, a.dinv[l] * rl, q1);
+        q2[0] = fmaf(rl, rl, q2[0]);
+        q2[1] = fmaf(rl, a.dinv[l] * rl, q2[1]);
       }
     }
-    double v2[2] = {q0, q1};
-    cluster_sum<2>(v2, &slots, parity, cl);
+    cluster_sum<2>(q2, &slots, tot, parity, cl);
     ++it;
-    rr = v2[0];
-    const double beta = v2[1] / rz;
-    rz = v2[1];
-    if (!isfinite(rr)) {
-      brk = 1;
-      break;
+    if (lead) {
+      rr = tot[0];
+      const double beta = tot[1] / rz;
+      rz = tot[1];
+      s_beta = (float)beta;
+      s_flag = !isfinite(rr) ? 2 : (rr <= tol2 ? 1 : 0);
     }
-    if (rr <= tol2) break;
-    const float bt = (float)beta;
+    __syncthreads();
+    if (s_flag != 0) break;
+    const float bt = s_beta;
     for (int64_t l = p0 + threadIdx.x; l < p1; l += CT) a.p[l] = fmaf(bt, a.p[l], a.dinv[l] * a.r[l]);
   }
   cl.sync();
-  if (rank == 0 && threadIdx.x == 0) {
+  if (rank == 0 && lead) {
     a.sc[S_ITER] = it;
     a.sc[S_TOTAL] += it;
     a.sc[S_RR] = rr;
     a.sc[S_BB] = bb;
-    a.sc[S_BREAK] = brk;
+    a.sc[S_BREAK] = s_flag == 2 ? 1 : 0;
     a.sc[S_DONE] = 1;
   }
 }
