@@ -14,40 +14,17 @@ struct ff {
   float h, l;
 };
 
-// double -> pair with integer operations only (GB300's FP64 pipe is slow, and
-// conversions run on it): hi keeps the top 24 significand bits of x
-// (truncation), lo = x - hi is the remaining 29-bit integer times 2^(e-1075),
-// rounded once to float. |x - hi - lo| <= 2^-48 |x|. Values below 2^-74 in
-// magnitude lose their lo part; |x| must stay below the FP32 range (~3e38).
+// double -> pair: hi = fl32(x), lo = fl32(x - hi). The conversions run on the
+// FP64 pipe, which is otherwise idle in this kernel, so they overlap with the
+// FP32 work (an integer-only split was measured slower: it adds instructions
+// to the FP32/ALU issue path, which is the kernel's limit).
 __device__ __forceinline__ ff ff_split(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e < 897) return {__int_as_float((int)sign), 0.f};          // |x| < 2^-126: flush
-  const unsigned hb = sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFF);
-  const unsigned mlo = (unsigned)(b & 0x1FFFFFFFu);
-  float lo = 0.f;
-  if (mlo != 0u && e >= 949) {
-    const float scale = __int_as_float((e - 1075 + 127) << 23);  // 2^(e - 1075)
-    lo = __fmul_rn(__uint2float_rn(mlo), scale);
-    if (sign) lo = -lo;
-  }
-  return {__int_as_float((int)hb), lo};
+  const float h = __double2float_rn(x);
+  const float l = __double2float_rn(x - (double)h);
+  return {h, l};
 }
 
-// float -> double by bit manipulation (exact for normal floats and zero)
-__device__ __forceinline__ double ff_f2d(float f) {
-  const unsigned fb = (unsigned)__float_as_int(f);
-  const unsigned e = (fb >> 23) & 0xFF;
-  if (e == 0) return __longlong_as_double((long long)((unsigned long long)(fb >> 31) << 63));  // +-0 (denormals flushed)
-  const unsigned long long db = ((unsigned long long)(fb >> 31) << 63) |
-                                ((unsigned long long)(e + 896) << 52) |
-                                ((unsigned long long)(fb & 0x7FFFFF) << 29);
-  return __longlong_as_double((long long)db);
-}
-
-// pair -> double: one FP64 addition of the exactly converted parts
-__device__ __forceinline__ double ff_join(ff a) { return __dadd_rn(ff_f2d(a.h), ff_f2d(a.l)); }
+__device__ __forceinline__ double ff_join(ff a) { return (double)a.h + (double)a.l; }
 
 // renormalise so that |l| <= ulp(h)/2 (TwoSum, valid for any magnitudes)
 __device__ __forceinline__ ff ff_norm(const ff a) {
