@@ -41,6 +41,7 @@ struct ArF64 {
   __device__ static V mul(V a, V b) { return a * b; }
   __device__ static V mac(V acc, V a, V b) { return fma(a, b, acc); }
   __device__ static V tidy(V a) { return a; }
+  __device__ static V tidy_before_add(V a) { return a; }
   static V host(double x) { return x; }
 };
 
@@ -49,7 +50,8 @@ struct ArPair {
   using V = ff;
   using GT = float2;
   __device__ static V in(const double* u, size_t i) { return ff_split(u[i]); }
-  __device__ static void out(double* w, size_t i, V v) { w[i] = ff_join(ff_norm(v)); }
+  // the FP64 addition in ff_join rounds hi + lo correctly without renormalising first
+  __device__ static void out(double* w, size_t i, V v) { w[i] = ff_join(v); }
   __device__ static V gl(const GT* G, size_t i) {
     const float2 g = G[i];
     return {g.x, g.y};
@@ -60,6 +62,8 @@ struct ArPair {
   __device__ static V mul(V a, V b) { return ff_mul(a, b); }
   __device__ static V mac(V acc, V a, V b) { return ff_mac(acc, a, b); }
   __device__ static V tidy(V a) { return ff_norm(a); }
+  // values that next enter the error-free additions of eo_apply need no renormalising
+  __device__ static V tidy_before_add(V a) { return a; }
   static V host(double x) { return ff_host_split(x); }
 };
 
@@ -80,12 +84,11 @@ struct Pad3 {
   static constexpr int ES = NP * PS;
 };
 
-// Blocks per SM requested from the register allocator: the pair kernel at
-// N = 7 is issue-bound at low occupancy, so it asks for five 192-thread blocks;
-// the FP64 kernel at N = 7 keeps four (72 registers).
+// Blocks per SM requested from the register allocator at N = 7: four 192-thread
+// blocks (at most 85 registers); five made the pair kernel spill and run slower.
 template <class Ar, int NP>
 __host__ __device__ constexpr int eo_min_blocks() {
-  return (Ar::kPairs && NP == 8) ? 5 : (NP == 8 ? 4 : 1);
+  return NP == 8 ? 4 : 1;
 }
 
 template <int NP>
@@ -197,9 +200,9 @@ __global__ void __launch_bounds__(NP* NP* eo_epb<NP>(), (eo_min_blocks<Ar, NP>()
         ws = Ar::mul(ws, hh);
         wt = Ar::mul(wt, hh);
       }
-      B[k * PS + j * RS + i] = Ar::tidy(wr);
-      Cc[k * PS + j * RS + i] = Ar::tidy(ws);
-      ut[k] = Ar::tidy(wt);
+      B[k * PS + j * RS + i] = Ar::tidy_before_add(wr);
+      Cc[k * PS + j * RS + i] = Ar::tidy_before_add(ws);
+      ut[k] = Ar::tidy_before_add(wt);
     }
   }
   __syncthreads();
