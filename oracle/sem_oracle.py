@@ -19,6 +19,7 @@ solver"), Section 2.3 ("Spectral Element Discretization"), Section 3.2
 * the gather-scatter QQ^T on global ids (the gs_op(+) interface, Section 3.2),
 * Jacobi-PCG, flexible PCG, Chebyshev-Jacobi smoothing and the p-multigrid
   V-cycle with orders N, N/2 .. 1 (Section 3.4),
+* projection of successive right-hand sides onto earlier solutions (Section 3.4),
 * the adjoint gradient of a mass-weighted loss with respect to nodal h1.
 
 Global (unique-node) vectors are used for every solver here; the library works
@@ -621,24 +622,27 @@ class SolveResult:
     history: list
 
 
-def pcg(apply, b, minv, tol: float, maxit: int, flexible: bool = False) -> SolveResult:
+def pcg(apply, b, minv, tol: float, maxit: int, flexible: bool = False, bnorm: float | None = None) -> SolveResult:
     """Preconditioned CG from x0 = 0 (Saad, Alg. 9.1), stopping when ||r||/||b|| <= tol.
 
     With ``flexible`` the Polak-Ribiere form beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k)
     is used (flexible CG, Section 3.4); otherwise
-    beta = (z_{k+1}, r_{k+1}) / (z_k, r_k).
+    beta = (z_{k+1}, r_{k+1}) / (z_k, r_k). ``bnorm`` replaces ||b|| in the stopping
+    test and the reported residuals (a projected solve measures its residual
+    against the norm of the right-hand side before projection).
     """
     x = np.zeros_like(b)
     r = b.copy()
-    bnorm = float(np.linalg.norm(b))
-    hist = [1.0]
-    if bnorm == 0.0:
-        return SolveResult(x, 0, 0.0, hist)
+    if bnorm is None:
+        bnorm = float(np.linalg.norm(b))
+    hist = [float(np.linalg.norm(b)) / bnorm if bnorm > 0.0 else 0.0]
+    if bnorm == 0.0 or hist[0] <= tol:
+        return SolveResult(x, 0, hist[0], hist)
     z = minv(r)
     p = z.copy()
     rz = float(r @ z)
     k = 0
-    relres = 1.0
+    relres = hist[0]
     while k < maxit:
         w = apply(p)
         alpha = rz / float(p @ w)
@@ -722,6 +726,94 @@ def solve(level: Level, b, h1=1.0, h2=0.0, tol=1e-8, maxit=1000, precond="jacobi
         res.mg = mg
         return res
     raise ValueError(precond)
+
+
+# ----------------------------------------------------------------------------
+# Projection of successive right-hand sides (Section 3.4, "projection-based
+# initial guesses"; Fischer, CMAME 163, 1998)
+# ----------------------------------------------------------------------------
+
+# A new direction is dropped when orthogonalisation leaves less than this
+# fraction of its squared A-norm (it lies in the span up to round-off).
+PROJ_DROP = 1e-20
+
+
+class Projection:
+    """Space of earlier solutions kept as an A-orthonormal basis x_1..x_l with
+    the products b_i = A x_i stored beside it.
+
+    project(b): for an A-orthonormal basis the A-norm-closest element of
+    span{x_i} to the solution x* of A x* = b is xbar = sum_i (x_i^T A x*) x_i =
+    sum_i (x_i, b) x_i, and its residual r0 = b - A xbar = b - sum_i (x_i, b) b_i
+    costs no operator application.
+
+    update(x, dx): after the solve of A dx = r0, the new direction is dx, or
+    the whole solution x when the basis already holds max_vectors (the basis
+    restarts from x alone). It is made A-orthogonal to the basis by classical
+    Gram-Schmidt applied twice, v <- v - sum_i (x_i, A v) x_i with A v carried
+    along as A v <- A v - sum_i (x_i, A v) b_i, then scaled to unit A-norm and
+    appended, unless it vanished (PROJ_DROP).
+    """
+
+    def __init__(self, apply, max_vectors: int):
+        self.apply = apply
+        self.max_vectors = max_vectors
+        self.X: list[np.ndarray] = []
+        self.AX: list[np.ndarray] = []
+
+    def project(self, b):
+        xbar = np.zeros_like(b)
+        r0 = b.copy()
+        for xi, bi in zip(self.X, self.AX):
+            a = float(xi @ b)
+            xbar = xbar + a * xi
+            r0 = r0 - a * bi
+        return xbar, r0
+
+    def update(self, x, dx):
+        if len(self.X) == self.max_vectors:
+            self.X, self.AX = [], []
+            v = x.copy()
+        else:
+            v = dx.copy()
+        w = self.apply(v)
+        n0 = float(v @ w)
+        for _ in range(2):
+            beta = [float(xi @ w) for xi in self.X]
+            for bt, xi, bi in zip(beta, self.X, self.AX):
+                v = v - bt * xi
+                w = w - bt * bi
+        n2 = float(v @ w)
+        if n2 > 0.0 and n2 > PROJ_DROP * n0:
+            s = 1.0 / np.sqrt(n2)
+            self.X.append(s * v)
+            self.AX.append(s * w)
+            return True
+        return False
+
+
+def solve_projected(level: Level, proj: Projection, b, h1=1.0, h2=0.0, tol=1e-8, maxit=1000,
+                    precond="jacobi", mg: "PMG | None" = None) -> SolveResult:
+    """Solve A x = b from the projected initial guess: xbar, r0 = proj.project(b);
+    A dx = r0 by PCG from zero (flexible PCG + p-MG when precond == "pmg"),
+    stopping at ||r|| <= tol ||b||; x = xbar + dx; proj.update(x, dx).
+    The result's relres0 is ||r0|| / ||b||."""
+    op = lambda v: level.apply(v, h1, h2)
+    bnorm = float(np.linalg.norm(b))
+    xbar, r0 = proj.project(b)
+    if precond == "jacobi":
+        dinv = np.where(level.free, 1.0 / level.diag(h1, h2), 0.0)
+        res = pcg(op, r0, lambda v: dinv * v, tol, maxit, bnorm=bnorm)
+    elif precond == "pmg":
+        res = pcg(op, r0, mg, tol, maxit, flexible=True, bnorm=bnorm)
+    else:
+        raise ValueError(precond)
+    x = xbar + res.x
+    res.added = proj.update(x, res.x)
+    res.relres0 = res.history[0]
+    res.xbar = xbar
+    res.x = x
+    return res
 
 
 # ----------------------------------------------------------------------------

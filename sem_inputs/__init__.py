@@ -183,6 +183,28 @@ def smooth_random_field(mesh: dict, seed: int, modes: int = 64, kmax: int = 4) -
     return g
 
 
+def travelling_field(mesh: dict, seed: int, t: float, modes: int = 32, kmax: int = 3,
+                     omega_max: float = 2.0 * np.pi) -> np.ndarray:
+    """g(x, t) = sum_m a_m cos(pi k_m . x + phi_m - omega_m t) at the mesh nodes:
+    a field that changes smoothly in time, standing in for the right-hand
+    sides of successive time steps. k_m, a_m and phi_m are drawn as in
+    smooth_random_field; omega_m ~ U[0, omega_max)."""
+    r = np.arange(-kmax, kmax + 1)
+    kk = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    n2 = (kk ** 2).sum(1)
+    kk = kk[(n2 > 0) & (n2 <= kmax * kmax)]
+    pick = (splitmix64(seed, np.arange(modes)) % np.uint64(len(kk))).astype(np.int64)
+    k = kk[pick].astype(np.float64)
+    a = np.sqrt(2.0 / modes) * normal(seed + 1, np.arange(modes))
+    phi = 2.0 * np.pi * uniform01(seed + 2, np.arange(modes))
+    omega = omega_max * uniform01(seed + 3, np.arange(modes))
+    g = np.zeros_like(mesh["x"])
+    for m in range(modes):
+        g += a[m] * np.cos(np.pi * (k[m, 0] * mesh["x"] + k[m, 1] * mesh["y"] + k[m, 2] * mesh["z"])
+                           + phi[m] - omega[m] * t)
+    return g
+
+
 def cube_for_points(N: int, target_points: int = 16_777_216) -> int:
     """Elements per side of the box whose local point count E*(N+1)^3 is closest to the target."""
     e1 = round((target_points / (N + 1) ** 3) ** (1.0 / 3.0))
