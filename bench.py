@@ -277,6 +277,56 @@ def solve_bench(ctx_cls, args, dev):
     return out
 
 
+def proj_bench(ctx_cls, args, dev):
+    """Successive right-hand sides f(x, t_k), t_k = 0.02 k (travelling waves), on the
+    24^3-element N=7 pressure problem: FCG + p-MG (FP32 smoother) to 1e-8 from x0 = 0
+    and from the projected initial guess (Section 3.4, projection-based initial guesses)."""
+    import torch
+
+    import sem_inputs as si
+    from paper_2104_05829_gb300 import Projection
+
+    mesh = si.box_mesh(args.solve_elements, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
+    ctx = ctx_cls.from_mesh(mesh)
+    modes, K, dt, nvec = 12, args.proj_steps, 0.02, 8
+    a, om, cm, sm = si.travelling_modes(mesh, 7, modes=modes, kmax=3)
+    cm = [torch.tensor(c.ravel(), device=dev) for c in cm]
+    sm = [torch.tensor(s.ravel(), device=dev) for s in sm]
+
+    def field(t):
+        f = torch.zeros_like(cm[0])
+        for m in range(modes):
+            f += a[m] * (cm[m] * np.cos(om[m] * t) + sm[m] * np.sin(om[m] * t))
+        return f
+
+    fs = [field(dt * k) for k in range(K)]
+    del cm, sm
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{args.solve_elements}^3 warped box, N=7, x=0 Dirichlet, {K} successive nodal RHS "
+                       f"f(x, 0.02k) ({modes} travelling waves), FCG + p-MG (FP32 smoother) to 1e-8",
+           "max_vectors": nvec}
+    ctx.solve(fs[0], tol=1e-8, maxit=300, precond="pmg", prec="fp32")   # warm-up and preconditioner setup
+    for name, proj in (("x0_zero", None), ("projected", Projection(ctx, nvec))):
+        times, iters, rel0 = [], [], []
+        for f in fs:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = ctx.solve(f, tol=1e-8, maxit=300, precond="pmg", prec="fp32", proj=proj)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            iters.append(info["iters"])
+            rel0.append(info.get("relres0", 1.0))
+        out[name] = {"mean_s": float(np.mean(times)), "mean_s_after_3": float(np.mean(times[3:])),
+                     "iters": iters, "relres0": rel0, "times_s": times}
+        if proj is not None:
+            proj.close()
+    ctx.close()
+    return out
+
+
 def sweep_orders(ctx_cls, dev, stream, steps=100):
     """Ax+gs throughput across orders at about 16.8M local points (nearest cube of elements)."""
     import torch
@@ -320,6 +370,8 @@ def main():
     ap.add_argument("--solve-variants", default="", help="comma list of fp64,fp32,bf16g,fp32_outer_pairs")
     ap.add_argument("--solve-48", action="store_true", help="also time the 48^3-element (56.6M-point) solve")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-proj", action="store_true", help="skip the successive-RHS projection sequence")
+    ap.add_argument("--proj-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--jacobi", action="store_true", help="also time Jacobi-PCG on the solve problem")
@@ -434,6 +486,8 @@ def main():
         line["sweep"] = sweep_orders(SemContext, dev, stream)
     if not args.no_solve:
         line["solve"] = solve_bench(SemContext, args, dev)
+    if not args.no_solve and not args.no_proj:
+        line["solve_proj"] = proj_bench(SemContext, args, dev)
     if args.solve_48:
         import copy
         a48 = copy.copy(args)

@@ -80,6 +80,8 @@ extern "C" {
 #define SEM_BUILD_PAIRS 4    /* (hi, lo) FP32 split of the FP64 factors for SEM_FP64P / SEM_AX_PAIRS */
 
 typedef struct sem_ctx sem_ctx;
+typedef struct sem_proj sem_proj;    /* projection space of earlier solutions (sem_proj_create) */
+#define SEM_PROJ_MAX 16              /* largest basis a projection space may keep */
 
 /* Mesh description (all HOST pointers, copied during sem_setup). */
 typedef struct {
@@ -121,6 +123,8 @@ typedef struct {
   int32_t coarse_iters;      /* total coarse-level PCG iterations (PMG only) */
   int32_t nlevels;
   double lmax[SEM_MAX_LEVELS]; /* Lanczos estimates of lambda_max(D^-1 A) per smoothed level */
+  double relres0;            /* sem_solve_proj: ||b - A xbar|| / ||b|| after projection; else -1 */
+  int32_t proj_count;        /* sem_solve_proj: basis size after the solve; else 0 */
 } sem_info;
 
 /* Per-level sizes. */
@@ -205,6 +209,44 @@ int sem_get_lmax(const sem_ctx* ctx, double* lmax, int n);
  * SEM_EINVAL, SEM_ECUDA. info may be NULL. */
 int sem_solve(sem_ctx* ctx, const double* f_L, const sem_coef* coef, double tol, int maxit, int precond,
               int prec, int rhs_flags, double* u_L, sem_info* info, void* stream);
+
+/* ---- Projection of successive right-hand sides (Section 3.4, "projection-based
+ * initial guesses"; Fischer, CMAME 163, 1998) ----
+ * A space keeps up to max_vectors earlier solution directions x_i, A-orthonormal
+ * (x_i^T A x_j = delta_ij, unique-node inner products), and b_i = A x_i beside
+ * them, as FP64 fine-level L-vectors in DEVICE memory the space owns
+ * (2 * max_vectors * nL * 8 bytes, allocated by sem_proj_create). A space
+ * belongs to one context and one operator: a solve or update with other
+ * coefficients (h1, h2, the h1_L pointer, SEM_OUTER_PAIRS) empties it first;
+ * a caller that changes the values behind h1_L must call sem_proj_reset. */
+int sem_proj_create(sem_ctx* ctx, int max_vectors, sem_proj** out);   /* 1 <= max_vectors <= SEM_PROJ_MAX */
+void sem_proj_free(sem_proj* pj);
+int sem_proj_reset(sem_proj* pj);                                     /* forget every vector */
+int sem_proj_count(const sem_proj* pj);                               /* vectors held (or SEM_EINVAL) */
+/* Read-only DEVICE pointers to x_i and b_i = A x_i, valid until the next update or free. */
+int sem_proj_vectors(const sem_proj* pj, int i, const double** x_L, const double** ax_L);
+/* xbar = sum_i (x_i, b) x_i, the A-norm-closest element of the span to A^-1 b,
+ * and r0 = b - sum_i (x_i, b) b_i = b - A xbar (no operator application).
+ * b_L: assembled, masked, replicated right-hand side. r0 may alias b; xbar may not.
+ * Asynchronous on `stream`. */
+int sem_proj_project(sem_proj* pj, const double* b_L, double* xbar_L, double* r0_L, void* stream);
+/* Add one direction: v = dx_L, or x_L when the space is full (it then restarts
+ * from x alone; x_L may be NULL, then dx_L is used). v is A-orthogonalised
+ * against the space by classical Gram-Schmidt applied twice (one FP64
+ * operator application A v, or the FP32-pair one with flags SEM_OUTER_PAIRS),
+ * scaled to unit A-norm and kept unless orthogonalisation left less than
+ * 1e-20 of its squared A-norm. *added (may be NULL) says whether it was kept.
+ * Synchronous (reads two norms). */
+int sem_proj_update(sem_proj* pj, const sem_coef* coef, int flags, const double* x_L, const double* dx_L,
+                    int* added, void* stream);
+/* sem_solve with the initial guess projected from the space: b is formed as in
+ * sem_solve, xbar and r0 = b - A xbar come from sem_proj_project, the Krylov
+ * solve finds dx from r0 with x0 = 0 and stops at ||r|| <= tol ||b|| (the
+ * unprojected b), u_L = xbar + dx, and the space takes the new direction
+ * (sem_proj_update). info->relres0 reports ||r0|| / ||b||. SEM_X0_GIVEN is
+ * rejected (SEM_EINVAL). Errors as sem_solve. */
+int sem_solve_proj(sem_ctx* ctx, sem_proj* pj, const double* f_L, const sem_coef* coef, double tol, int maxit,
+                   int precond, int prec, int rhs_flags, double* u_L, sem_info* info, void* stream);
 
 /* Adjoint gradient with respect to nodal h1 (no counterpart in the paper's
  * solver; built on eq. Ae): g_L = -sum_{m,m'} (D_m lam)(G_mm')(D_m' u) at every

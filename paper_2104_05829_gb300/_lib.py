@@ -48,7 +48,7 @@ class SemCoef(C.Structure):
 class SemInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double), ("bnorm", C.c_double),
                 ("coarse_iters", C.c_int32), ("nlevels", C.c_int32),
-                ("lmax", C.c_double * SEM_MAX_LEVELS)]
+                ("lmax", C.c_double * SEM_MAX_LEVELS), ("relres0", C.c_double), ("proj_count", C.c_int32)]
 
 
 class SemLevelDesc(C.Structure):
@@ -82,6 +82,14 @@ SIGNATURES = {
     "sem_vcycle": (_I, [_P, _P, _P, _P]),
     "sem_get_lmax": (_I, [_P, _P, _I]),
     "sem_solve": (_I, [_P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),
+    "sem_solve_proj": (_I, [_P, _P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),
+    "sem_proj_create": (_I, [_P, _I, C.POINTER(_P)]),
+    "sem_proj_free": (None, [_P]),
+    "sem_proj_reset": (_I, [_P]),
+    "sem_proj_count": (_I, [_P]),
+    "sem_proj_vectors": (_I, [_P, _I, C.POINTER(_P), C.POINTER(_P)]),
+    "sem_proj_project": (_I, [_P, _P, _P, _P, _P]),
+    "sem_proj_update": (_I, [_P, C.POINTER(SemCoef), _I, _P, _P, C.POINTER(_I), _P]),
     "sem_grad_h1": (_I, [_P, _P, _P, _P, _I, _P]),
     "sem_rhs": (_I, [_P, _P, _P, _P]),
     "sem_mass_local": (_I, [_P, _P, _P, _P]),

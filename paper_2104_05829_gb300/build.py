@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsem.so")
-SOURCES = ["setup.cu", "gsmap.cu", "ax.cu", "ax_eo.cu", "gs.cu", "blas.cu", "solve.cu", "coarse.cu", "dot_static.cu"]
+SOURCES = ["setup.cu", "gsmap.cu", "ax.cu", "ax_eo.cu", "gs.cu", "blas.cu", "solve.cu", "coarse.cu", "dot_static.cu",
+           "proj.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -32,7 +33,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "sem_internal.cuh"), os.path.join(INCLUDE, "sem.h")]
+    files += [os.path.join(CSRC, h) for h in sorted(os.listdir(CSRC)) if h.endswith(".cuh")]
+    files += [os.path.join(INCLUDE, "sem.h")]
     return files
 
 

@@ -11,81 +11,14 @@
 // Scalars (alpha, beta, residual norms) live in a device array `sc` so that a
 // whole iteration runs without the host; sc[S_DONE] != 0 turns every kernel
 // of that loop into a no-op (device-side convergence).
+#include "reduce.cuh"
 #include "sem_internal.cuh"
 
 namespace sem {
 
 namespace {
 
-template <int NS>
-struct Sums {
-  double v[NS];
-};
-
-template <int NS>
-__device__ __forceinline__ void warp_sum(Sums<NS>& a) {
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a.v[s] += __shfl_xor_sync(0xffffffffu, a.v[s], o);
-}
-
-// Block-reduce `a`, publish the block partial, and let the last block combine
-// all partials in index order and call fin(totals).
-template <int NS, class Fin>
-__device__ void reduce_finish(Sums<NS> a, double* part, unsigned* ticket, Fin fin) {
-  __shared__ double s_w[RED_THREADS / 32][NS];
-  __shared__ bool s_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  warp_sum(a);
-  if (lane == 0)
-#pragma unroll
-    for (int s = 0; s < NS; ++s) s_w[warp][s] = a.v[s];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      double t = 0;
-      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
-      part[s * gridDim.x + blockIdx.x] = t;
-    }
-    __threadfence();
-    const unsigned t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  Sums<NS> b;
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    double t = 0;
-    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(part + s * gridDim.x + q);
-    b.v[s] = t;
-  }
-  warp_sum(b);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int s = 0; s < NS; ++s) s_w[warp][s] = b.v[s];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Sums<NS> tot;
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      double t = 0;
-      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
-      tot.v[s] = t;
-    }
-    fin(tot);
-    *ticket = 0u;
-  }
-}
-
 __device__ __forceinline__ bool skip(const double* sc) { return sc && sc[S_DONE] != 0.0; }
-
-#define GRID_LOOP(l, n) \
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (n); l += (int64_t)gridDim.x * blockDim.x)
 
 // ---- plain dot ---------------------------------------------------------------
 template <typename T>
@@ -100,11 +33,13 @@ __global__ void __launch_bounds__(RED_THREADS)
 }
 
 // ---- PCG start: r = b (- w), x = 0 unless given, p = dinv r; (b,b), (r, dinv r) ----
+// bbref (device, may be null) replaces (b,b) as the reference norm^2 of the
+// stopping test (a projected solve measures against the unprojected b).
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
     k_pcg_begin(int64_t n, const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ x, T* __restrict__ r,
                 const T* __restrict__ dinv, T* __restrict__ p, const uint8_t* __restrict__ own, double* part,
-                unsigned* ticket, double* sc, double tol) {
+                unsigned* ticket, double* sc, double tol, const double* bbref) {
   Sums<3> acc{{0, 0, 0}};
   GRID_LOOP(l, n) {
     const T bl = b[l];
@@ -121,13 +56,14 @@ __global__ void __launch_bounds__(RED_THREADS)
     }
   }
   reduce_finish<3>(acc, part, ticket, [=] __device__(const Sums<3>& t) {
-    sc[S_BB] = t.v[0];
+    const double bb = bbref ? *bbref : t.v[0];
+    sc[S_BB] = bb;
     sc[S_RZ] = t.v[1];
     sc[S_RR] = t.v[2];
-    sc[S_TOL2] = tol * tol * t.v[0];
+    sc[S_TOL2] = tol * tol * bb;
     sc[S_ITER] = 0;
     sc[S_BREAK] = 0;
-    sc[S_DONE] = (t.v[2] <= tol * tol * t.v[0]) ? 1.0 : 0.0;
+    sc[S_DONE] = (t.v[2] <= tol * tol * bb) ? 1.0 : 0.0;
   });
 }
 
@@ -368,15 +304,15 @@ int mul_counting_weight(const Level& L, int prec, const void* in, void* out, cud
 }
 
 int pcg_begin_tol(Ctx& C, const Level& L, int prec, const void* b, const void* w, void* x, void* r,
-                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s) {
+                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s, const double* bbref) {
   if (prec == SEM_FP64)
     k_pcg_begin<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
                                                            (double*)r, (const double*)dinv, (double*)p, L.owner,
-                                                           C.red_part, C.red_ticket, sc, tol);
+                                                           C.red_part, C.red_ticket, sc, tol, bbref);
   else
     k_pcg_begin<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x,
                                                           (float*)r, (const float*)dinv, (float*)p, L.owner,
-                                                          C.red_part, C.red_ticket, sc, tol);
+                                                          C.red_part, C.red_ticket, sc, tol, bbref);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }

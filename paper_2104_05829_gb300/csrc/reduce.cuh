@@ -1,0 +1,82 @@
+// Deterministic block reductions shared by the vector kernels (blas.cu, proj.cu).
+//
+// A fixed grid of RED_BLOCKS blocks walks the vector with a fixed stride; each
+// block reduces its NS running sums in a fixed shuffle tree and stores them in
+// part[s * gridDim.x + blockIdx.x]; the last block to finish (atomic ticket)
+// adds the block partials in index order and calls fin(totals). The result
+// does not depend on block scheduling. Nothing spins.
+#pragma once
+
+#include "sem_internal.cuh"
+
+namespace sem {
+
+template <int NS>
+struct Sums {
+  double v[NS];
+};
+
+template <int NS>
+__device__ __forceinline__ void warp_sum(Sums<NS>& a) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a.v[s] += __shfl_xor_sync(0xffffffffu, a.v[s], o);
+}
+
+// Block-reduce `a`, publish the block partial, and let the last block combine
+// all partials in index order and call fin(totals).
+template <int NS, class Fin>
+__device__ void reduce_finish(Sums<NS> a, double* part, unsigned* ticket, Fin fin) {
+  __shared__ double s_w[RED_THREADS / 32][NS];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  warp_sum(a);
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = a.v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
+      part[s * gridDim.x + blockIdx.x] = t;
+    }
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  Sums<NS> b;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double t = 0;
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(part + s * gridDim.x + q);
+    b.v[s] = t;
+  }
+  warp_sum(b);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = b.v[s];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Sums<NS> tot;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int w = 0; w < RED_THREADS / 32; ++w) t += s_w[w][s];
+      tot.v[s] = t;
+    }
+    fin(tot);
+    *ticket = 0u;
+  }
+}
+
+#define GRID_LOOP(l, n) \
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (n); l += (int64_t)gridDim.x * blockDim.x)
+
+}  // namespace sem

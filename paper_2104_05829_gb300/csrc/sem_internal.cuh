@@ -178,7 +178,8 @@ int mul_counting_weight(const Level& L, int prec, const void* in, void* out, cud
 
 // Krylov / smoother kernels (blas.cu)
 int pcg_begin_tol(Ctx& C, const Level& L, int prec, const void* b, const void* w, void* x, void* r,
-                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s);
+                  const void* dinv, void* p, double* sc, double tol, cudaStream_t s,
+                  const double* bbref = nullptr);
 int kr_alpha(Ctx& C, const Level& L, int prec, const void* p, const void* w, double* sc, cudaStream_t s);
 int kr_update_jacobi(Ctx& C, const Level& L, int prec, void* x, const void* p, void* r, const void* w,
                      const void* dinv, double* sc, cudaStream_t s);
@@ -194,6 +195,17 @@ int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, 
 int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, void* d, double c1, double c2,
               cudaStream_t s);
 int residual_weighted(const Level& L, int prec, const void* b, const void* w, void* out, cudaStream_t s);
+
+// ---- proj.cu: projection of successive right-hand sides
+struct Proj;
+void proj_bind_coef(Proj& P, const sem_coef* c, bool pairs);
+int proj_project(Proj& P, const double* b, double* xbar, double* r0, cudaStream_t s);
+int proj_update(Proj& P, const sem_coef* c, bool pairs, const double* x, const double* dx, int* added,
+                cudaStream_t s);
+int proj_add_xbar(Proj& P, double* u, cudaStream_t s);
+int proj_state(const Proj& P, int* count, int* maxv, double** xbar, const double** bb_dev, double* h_bb_rr0,
+               cudaStream_t s);
+bool proj_belongs(const Proj& P, const Ctx* C);
 
 // ---- solve.cu
 int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s);

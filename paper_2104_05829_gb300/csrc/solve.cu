@@ -503,14 +503,22 @@ int sem_grad_h1(sem_ctx* h, const double* u, const double* lam, double* g, int f
   return SEM_OK;
 }
 
-int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int maxit, int precond, int prec,
-              int rhs_flags, double* u, sem_info* info, void* stream) {
-  Ctx* C = ctx_of(h);
+}  // extern "C"
+
+namespace {
+
+// The body of sem_solve and sem_solve_proj. With a projection space P the
+// right-hand side b is first projected (xbar, r0 = b - A xbar), the Krylov solve
+// finds dx from r0 with x0 = 0 and stops at ||r|| <= tol ||b||, and afterwards
+// u = xbar + dx and the space takes the new direction.
+int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, int maxit, int precond, int prec,
+               int rhs_flags, double* u, sem_info* info, cudaStream_t s) {
   SEM_TRY(check_level(C, 0));
   if (!f || !c || !u || f == u || !(tol >= 0.0) || maxit < 0 ||
       (precond != SEM_PC_JACOBI && precond != SEM_PC_PMG) ||
-      (rhs_flags & ~(SEM_RHS_ASSEMBLED | SEM_X0_GIVEN | SEM_OUTER_PAIRS))) {
-    set_detail("sem_solve: bad argument");
+      (rhs_flags & ~(SEM_RHS_ASSEMBLED | SEM_X0_GIVEN | SEM_OUTER_PAIRS)) ||
+      (P && (rhs_flags & SEM_X0_GIVEN))) {
+    set_detail("sem_solve: bad argument (a projected solve takes no initial guess)");
     return SEM_EINVAL;
   }
   if (precond == SEM_PC_PMG) SEM_TRY(check_prec(C, 0, prec));
@@ -529,7 +537,6 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
     else SEM_TRY(ax_apply(C->lev[0], SEM_FP64, in, out, c->h1, c->h2, c->h1_L, st, skip));
     return gs_apply_skip(C->lev[0], SEM_FP64, out, true, skip, st);
   };
-  cudaStream_t s = (cudaStream_t)stream;
   Level& L = C->lev[0];
   const int64_t n = L.nL;
   double* sc = C->scal;   // outer slot set
@@ -542,6 +549,14 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
     SEM_TRY(rhs_mass(L, f, b, s));
   }
   SEM_TRY(gs_apply(L, SEM_FP64, b, true, s));
+  // projection onto earlier solutions: b <- r0 = b - A xbar (in place), reference norm (b, b)
+  const double* bbref = nullptr;
+  double* xbar = nullptr;
+  if (P) {
+    proj_bind_coef(*P, c, pairs);
+    SEM_TRY(proj_state(*P, nullptr, nullptr, &xbar, &bbref, nullptr, s));
+    SEM_TRY(proj_project(*P, b, xbar, b, s));
+  }
   const bool x0 = (rhs_flags & SEM_X0_GIVEN) != 0;
   double* w = C->w;
   if (x0) SEM_TRY(outer_ax(u, w, nullptr, s));
@@ -552,7 +567,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
   if (precond == SEM_PC_JACOBI) {
     double* dinv = C->z;
     SEM_TRY(level_dinv(*C, 0, c->h1, c->h2, c->h1_L, dinv, nullptr, s));
-    SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, dinv, C->p, sc, tol, s));
+    SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, dinv, C->p, sc, tol, s, bbref));
     const int batch = 8;
     int launched = 0;
     while (true) {
@@ -582,7 +597,7 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
   } else {
     if (!C->pc_ready || C->pc_h1 != c->h1 || C->pc_h2 != c->h2 || C->pc_prec != prec)
       SEM_TRY(precond_setup(*C, c->h1, c->h2, prec, s));
-    SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, nullptr, nullptr, sc, tol, s));
+    SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, nullptr, nullptr, sc, tol, s, bbref));
     SEM_CUDA_TRY(cudaMemsetAsync(C->p, 0, n * 8, s));
     SEM_CUDA_TRY(cudaMemsetAsync(C->dr, 0, n * 8, s));
     SEM_TRY(read_scalars(*C, 0, s));
@@ -612,6 +627,27 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
       if (rc == SEM_OK && C->h_scal[S_DONE] == 0.0) rc = SEM_ENOTCONV;
     }
   }
+  double relres0 = -1.0;
+  int pcount = 0;
+  if (P) {
+    // u holds dx: store it as the new direction (on restart the whole x is stored instead), then u = xbar + dx
+    int count = 0, maxv = 0;
+    SEM_TRY(proj_state(*P, &count, &maxv, nullptr, nullptr, nullptr, s));
+    if (rc == SEM_OK || rc == SEM_ENOTCONV) {
+      if (count < maxv) {
+        SEM_TRY(proj_update(*P, c, pairs, nullptr, u, nullptr, s));
+        SEM_TRY(proj_add_xbar(*P, u, s));
+      } else {
+        SEM_TRY(proj_add_xbar(*P, u, s));
+        SEM_TRY(proj_update(*P, c, pairs, u, u, nullptr, s));
+      }
+    } else {
+      SEM_TRY(proj_add_xbar(*P, u, s));
+    }
+    double h[2] = {0, 0};
+    SEM_TRY(proj_state(*P, &pcount, nullptr, nullptr, nullptr, h, s));
+    relres0 = h[0] > 0 ? std::sqrt(h[1] / h[0]) : 0.0;
+  }
   if (info) {
     double ct = 0;
     SEM_CUDA_TRY(cudaMemcpyAsync(&ct, C->scal + 1 * S_NSLOTS + S_TOTAL, 8, cudaMemcpyDeviceToHost, s));
@@ -622,10 +658,31 @@ int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int ma
     info->coarse_iters = (int)ct;
     info->nlevels = C->nlevels;
     for (int l = 0; l < SEM_MAX_LEVELS; ++l) info->lmax[l] = (l < C->nlevels) ? C->lev[l].lmax : 0.0;
+    info->relres0 = relres0;
+    info->proj_count = pcount;
   }
   if (rc == SEM_ENOTCONV) set_detail("no convergence in %d iterations (relres %.3e)", maxit, bb > 0 ? std::sqrt(rr / bb) : 0.0);
   if (rc == SEM_EBREAKDOWN) set_detail("Krylov breakdown after %d iterations", iters);
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sem_solve(sem_ctx* h, const double* f, const sem_coef* c, double tol, int maxit, int precond, int prec,
+              int rhs_flags, double* u, sem_info* info, void* stream) {
+  return solve_impl(ctx_of(h), nullptr, f, c, tol, maxit, precond, prec, rhs_flags, u, info, (cudaStream_t)stream);
+}
+
+int sem_solve_proj(sem_ctx* h, sem_proj* pj, const double* f, const sem_coef* c, double tol, int maxit,
+                   int precond, int prec, int rhs_flags, double* u, sem_info* info, void* stream) {
+  Proj* P = reinterpret_cast<Proj*>(pj);
+  if (!P || !proj_belongs(*P, ctx_of(h))) {
+    set_detail("sem_solve_proj: NULL projection space or a space created for another context");
+    return SEM_EINVAL;
+  }
+  return solve_impl(ctx_of(h), P, f, c, tol, maxit, precond, prec, rhs_flags, u, info, (cudaStream_t)stream);
 }
 
 }  // extern "C"

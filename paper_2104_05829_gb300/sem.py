@@ -218,7 +218,8 @@ class SemContext:
 
     # ---- solve -----------------------------------------------------------------
     def solve(self, f, h1=1.0, h2=0.0, h1_L=None, tol=1e-8, maxit=1000, precond="jacobi", prec="fp64",
-              rhs="nodal", x0=None, u=None, outer_pairs=False, stream=None, raise_on_error=True):
+              rhs="nodal", x0=None, u=None, outer_pairs=False, stream=None, raise_on_error=True, proj=None):
+        """sem_solve, or sem_solve_proj when a Projection space `proj` is given."""
         n = self.nL
         if u is None:
             u = torch.empty_like(f) if x0 is None else x0.clone()
@@ -228,13 +229,19 @@ class SemContext:
         flags |= L.SEM_OUTER_PAIRS if outer_pairs else 0
         c = L.SemCoef(float(h1), float(h2), _dev(h1_L, torch.float64, n, "h1_L") if h1_L is not None else None)
         info = L.SemInfo()
-        rc = self._lib.sem_solve(self._h, _dev(f, torch.float64, n, "f"), C.byref(c), float(tol), int(maxit),
-                                 _PC[precond], _PREC[prec], flags, _dev(u, torch.float64, n, "u"), C.byref(info),
-                                 _stream(stream))
+        args = (_dev(f, torch.float64, n, "f"), C.byref(c), float(tol), int(maxit), _PC[precond], _PREC[prec], flags,
+                _dev(u, torch.float64, n, "u"), C.byref(info), _stream(stream))
+        if proj is None:
+            rc = self._lib.sem_solve(self._h, *args)
+        else:
+            rc = self._lib.sem_solve_proj(self._h, proj._h, *args)
         out = {"iters": info.iters, "relres": info.relres, "bnorm": info.bnorm, "coarse_iters": info.coarse_iters,
                "lmax": [info.lmax[i] for i in range(max(0, info.nlevels - 1))], "status": rc}
+        if proj is not None:
+            out["relres0"] = info.relres0
+            out["proj_count"] = info.proj_count
         if raise_on_error:
-            L.check(rc, "sem_solve")
+            L.check(rc, "sem_solve_proj" if proj is not None else "sem_solve")
         return u, out
 
     # ---- read-back -------------------------------------------------------------
@@ -271,6 +278,74 @@ class SemContext:
         out = [np.empty(d["nL"], np.float64) for _ in range(3)] + [np.empty(d["nL"], np.int64)]
         L.check(self._lib.sem_get_coords(self._h, level, *[a.ctypes.data for a in out]), "sem_get_coords")
         return out
+
+
+class Projection:
+    """A projection space of earlier solutions (sem_proj_*): A-orthonormal
+    directions x_i with A x_i beside them, used by SemContext.solve(proj=...)."""
+
+    def __init__(self, ctx: SemContext, max_vectors: int = 8):
+        self._lib = L.load()
+        self.ctx = ctx
+        h = C.c_void_p()
+        L.check(self._lib.sem_proj_create(ctx._h, int(max_vectors), C.byref(h)), "sem_proj_create")
+        self._h = h
+        self.max_vectors = int(max_vectors)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sem_proj_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        L.check(self._lib.sem_proj_reset(self._h), "sem_proj_reset")
+
+    def __len__(self) -> int:
+        n = self._lib.sem_proj_count(self._h)
+        if n < 0:
+            L.check(n, "sem_proj_count")
+        return n
+
+    def vectors(self, i: int):
+        """(x_i, A x_i) copied into new CUDA tensors (read-back for validation)."""
+        px, pa = C.c_void_p(), C.c_void_p()
+        L.check(self._lib.sem_proj_vectors(self._h, int(i), C.byref(px), C.byref(pa)), "sem_proj_vectors")
+        n = self.ctx.nL
+        return (torch.as_tensor(_DeviceView(px.value, n), device="cuda").clone(),
+                torch.as_tensor(_DeviceView(pa.value, n), device="cuda").clone())
+
+    def project(self, b, xbar=None, r0=None, stream=None):
+        n = self.ctx.nL
+        xbar = torch.empty_like(b) if xbar is None else xbar
+        r0 = torch.empty_like(b) if r0 is None else r0
+        L.check(self._lib.sem_proj_project(self._h, _dev(b, torch.float64, n, "b"), _dev(xbar, torch.float64, n, "xbar"),
+                                           _dev(r0, torch.float64, n, "r0"), _stream(stream)), "sem_proj_project")
+        return xbar, r0
+
+    def update(self, dx, x=None, h1=1.0, h2=0.0, outer_pairs=False, stream=None) -> bool:
+        n = self.ctx.nL
+        c = L.SemCoef(float(h1), float(h2), None)
+        added = C.c_int(0)
+        L.check(self._lib.sem_proj_update(self._h, C.byref(c), L.SEM_OUTER_PAIRS if outer_pairs else 0,
+                                          _dev(x, torch.float64, n, "x") if x is not None else None,
+                                          _dev(dx, torch.float64, n, "dx"), C.byref(added), _stream(stream)),
+                "sem_proj_update")
+        return bool(added.value)
+
+
+class _DeviceView:
+    """View of n doubles at a library-owned device address (CUDA array interface); callers
+    only copy from it (torch does not accept the interface's read-only flag)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 2,
+                                         "strides": None}
 
 
 def gll(N: int):

@@ -183,12 +183,11 @@ def smooth_random_field(mesh: dict, seed: int, modes: int = 64, kmax: int = 4) -
     return g
 
 
-def travelling_field(mesh: dict, seed: int, t: float, modes: int = 32, kmax: int = 3,
-                     omega_max: float = 2.0 * np.pi) -> np.ndarray:
-    """g(x, t) = sum_m a_m cos(pi k_m . x + phi_m - omega_m t) at the mesh nodes:
-    a field that changes smoothly in time, standing in for the right-hand
-    sides of successive time steps. k_m, a_m and phi_m are drawn as in
-    smooth_random_field; omega_m ~ U[0, omega_max)."""
+def travelling_modes(mesh: dict, seed: int, modes: int = 32, kmax: int = 3, omega_max: float = 2.0 * np.pi):
+    """The pieces of travelling_field: amplitudes a_m, frequencies omega_m and the
+    nodal fields cos(theta_m), sin(theta_m) with theta_m = pi k_m . x + phi_m,
+    so that g(x, t) = sum_m a_m (cos(theta_m) cos(omega_m t) + sin(theta_m) sin(omega_m t)).
+    k_m, a_m and phi_m are drawn as in smooth_random_field; omega_m ~ U[0, omega_max)."""
     r = np.arange(-kmax, kmax + 1)
     kk = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
     n2 = (kk ** 2).sum(1)
@@ -198,10 +197,19 @@ def travelling_field(mesh: dict, seed: int, t: float, modes: int = 32, kmax: int
     a = np.sqrt(2.0 / modes) * normal(seed + 1, np.arange(modes))
     phi = 2.0 * np.pi * uniform01(seed + 2, np.arange(modes))
     omega = omega_max * uniform01(seed + 3, np.arange(modes))
+    theta = [np.pi * (k[m, 0] * mesh["x"] + k[m, 1] * mesh["y"] + k[m, 2] * mesh["z"]) + phi[m] for m in range(modes)]
+    return a, omega, [np.cos(t) for t in theta], [np.sin(t) for t in theta]
+
+
+def travelling_field(mesh: dict, seed: int, t: float, modes: int = 32, kmax: int = 3,
+                     omega_max: float = 2.0 * np.pi) -> np.ndarray:
+    """g(x, t) = sum_m a_m cos(pi k_m . x + phi_m - omega_m t) at the mesh nodes:
+    a field that changes smoothly in time, standing in for the right-hand
+    sides of successive time steps (travelling_modes gives its pieces)."""
+    a, omega, c, s = travelling_modes(mesh, seed, modes, kmax, omega_max)
     g = np.zeros_like(mesh["x"])
     for m in range(modes):
-        g += a[m] * np.cos(np.pi * (k[m, 0] * mesh["x"] + k[m, 1] * mesh["y"] + k[m, 2] * mesh["z"])
-                           + phi[m] - omega[m] * t)
+        g += a[m] * (c[m] * np.cos(omega[m] * t) + s[m] * np.sin(omega[m] * t))
     return g
 
 

@@ -81,3 +81,17 @@ def test_setup_argument_validation_on_host(lib):
     m = L.SemMesh(0, 1, x.ctypes.data, x.ctypes.data, x.ctypes.data, g.ctypes.data, None)
     assert lib.sem_setup(C.byref(m), None, C.byref(h)) == L.SEM_EINVAL
     assert not h.value
+
+
+def test_projection_entry_points_reject_null_on_host(lib):
+    import ctypes as C
+    from paper_2104_05829_gb300 import _lib as L
+    h = C.c_void_p()
+    assert lib.sem_proj_create(None, 4, C.byref(h)) == L.SEM_EINVAL and not h.value
+    assert lib.sem_proj_count(None) == L.SEM_EINVAL
+    assert lib.sem_proj_reset(None) == L.SEM_EINVAL
+    assert lib.sem_proj_vectors(None, 0, None, None) == L.SEM_EINVAL
+    assert lib.sem_proj_project(None, None, None, None, None) == L.SEM_EINVAL
+    assert lib.sem_proj_update(None, None, 0, None, None, None, None) == L.SEM_EINVAL
+    assert lib.sem_solve_proj(None, None, None, None, 1e-8, 10, 0, 0, 0, None, None, None) == L.SEM_EINVAL
+    lib.sem_proj_free(None)
