@@ -542,6 +542,251 @@ def build_levels(mesh: dict, orders=None):
 
 
 # ----------------------------------------------------------------------------
+# Overlapping additive Schwarz smoother with fast-diagonalisation local solves
+# (Section 3.4: ASM on extended elements of (N+3)^3 points, local solves by
+# tensor-product fast diagonalisation in about 12 E (N+3)^4 operations; the
+# method of Lynch, Rice and Thomas (1964) as used for spectral elements by
+# Deville, Fischer and Mund (2002) and Lottes and Fischer (2005))
+# ----------------------------------------------------------------------------
+
+# face-side boundary types of the 1-D extended segment
+SCH_NB, SCH_DIR, SCH_NEU = 0, 1, 2
+
+
+def fdm_1d(N: int, left: int, right: int):
+    """Reference (element length 2) 1-D data of the extended segment of an element.
+
+    The segment is the element's N+1 GLL nodes plus one node on each side: the
+    first interior node of the neighbouring element, taken as an element of the
+    same length (SCH_NB). The 1-D stiffness K = D^T diag(rho) D and mass
+    diag(rho) of the (up to) three elements are assembled and restricted to the
+    segment's nodes, i.e. homogeneous Dirichlet conditions one node beyond the
+    overlap. A side on a Dirichlet boundary (SCH_DIR) drops the boundary node
+    and the extension node; a Neumann side (SCH_NEU) keeps the boundary node and
+    has no extension node.
+
+    Returns S (N+3, N+3) and lam (N+3): S^T B S = I and S^T A S = diag(lam) on
+    the present slots (slot s = extended index + 1, extended index -1..N+1);
+    rows of absent slots and the unused columns are zero (their lam is 1).
+    """
+    _, rho = gll(N)
+    D = deriv_matrix(N)
+    K = D.T @ np.diag(rho) @ D
+    n = 3 * N + 1
+    A = np.zeros((n, n))
+    Bd = np.zeros(n)
+    for el, present in ((0, left == SCH_NB), (1, True), (2, right == SCH_NB)):
+        if present:
+            sl = slice(el * N, el * N + N + 1)
+            A[sl, sl] += K
+            Bd[sl] += rho
+    slots = []
+    for ext in range(-1, N + 2):
+        if ext == -1 and left != SCH_NB:
+            continue
+        if ext == 0 and left == SCH_DIR:
+            continue
+        if ext == N and right == SCH_DIR:
+            continue
+        if ext == N + 1 and right != SCH_NB:
+            continue
+        slots.append(ext)
+    g = np.array([N + ext for ext in slots])
+    As = A[np.ix_(g, g)]
+    bs = Bd[g]
+    # A s = lam B s with B diagonal: symmetric form B^-1/2 A B^-1/2 = Q diag(lam) Q^T, S = B^-1/2 Q
+    isq = 1.0 / np.sqrt(bs)
+    lam, Q = np.linalg.eigh(isq[:, None] * As * isq[None, :])
+    S = np.zeros((N + 3, N + 3))
+    lam_full = np.ones(N + 3)
+    S[np.array(slots) + 1, : len(slots)] = isq[:, None] * Q
+    lam_full[: len(slots)] = lam
+    return S, lam_full
+
+
+def element_lengths(level: "Level") -> np.ndarray:
+    """(E, 3) lengths of each element along r, s, t: the mean, over the (N+1)^2
+    grid lines in that direction, of the distance between the line's end nodes."""
+    X = np.stack([level.x, level.y, level.z])          # (3, E, k, j, i)
+    N = level.N
+    Lr = np.sqrt(((X[..., N] - X[..., 0]) ** 2).sum(0)).mean(axis=(1, 2))
+    Ls = np.sqrt(((X[..., N, :] - X[..., 0, :]) ** 2).sum(0)).mean(axis=(1, 2))
+    Lt = np.sqrt(((X[:, :, N] - X[:, :, 0]) ** 2).sum(0)).mean(axis=(1, 2))
+    return np.stack([Lr, Ls, Lt], 1)
+
+
+def face_points(N: int, f: int):
+    """Local (i, j, k) of face f (2d + side: d = 0 r, 1 s, 2 t; side 0 at index 0,
+    side 1 at index N) as arrays indexed [a, b], with (a, b) the two other
+    indices in r, s, t order."""
+    d, side = divmod(f, 2)
+    a, b = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    c = np.full_like(a, side * N)
+    ijk = [None, None, None]
+    ijk[d] = c
+    others = [q for q in range(3) if q != d]
+    ijk[others[0]] = a
+    ijk[others[1]] = b
+    return ijk
+
+
+@dataclass
+class Schwarz:
+    """Per-level data of the Schwarz smoother.
+
+    layer[e, f, a, b]: unique node of the face-layer slot of face f of element e
+    at face position (a, b) -- the node one step inside the neighbouring element
+    from the shared face node -- or -1 when the face has no neighbour.
+    btype[e, f]: SCH_NB, SCH_DIR or SCH_NEU. L[e]: element lengths (r, s, t).
+    W: 1 / (number of subdomain slots holding each unique node), 0 at Dirichlet nodes.
+    """
+    layer: np.ndarray
+    btype: np.ndarray
+    L: np.ndarray
+    W: np.ndarray
+    fdm: dict
+
+
+def schwarz_setup(level: "Level") -> Schwarz:
+    """Face-layer maps from the node numbering: the neighbour across face f is the
+    other element holding the face's centre node; in that element the face is
+    the one on which all of the face's nodes lie, and each layer node is one
+    step from the face along that element's face-normal index."""
+    N, E = level.N, level.E
+    if N < 2:
+        raise ValueError("the Schwarz smoother needs N >= 2")
+    NP = N + 1
+    node = level.node.reshape(E, NP, NP, NP)           # [e, k, j, i]
+    holders = {}
+    for e in range(E):
+        for loc, g in enumerate(node[e].ravel()):
+            holders.setdefault(int(g), []).append((e, loc))
+    layer = -np.ones((E, 6, NP, NP), dtype=np.int64)
+    btype = np.zeros((E, 6), dtype=np.int64)
+    for e in range(E):
+        for f in range(6):
+            i, j, k = face_points(N, f)
+            fn = node[e][k, j, i]                       # face nodes [a, b]
+            centre = int(fn[1, 1])
+            other = [h for h in holders[centre] if h[0] != e]
+            if not other:
+                btype[e, f] = SCH_DIR if level.dir_g[centre] else SCH_NEU
+                continue
+            btype[e, f] = SCH_NB
+            e2 = other[0][0]
+            loc2 = {int(g): l for l, g in enumerate(node[e2].ravel())}
+            pos = np.array([[np.unravel_index(loc2[int(g)], (NP, NP, NP)) for g in row] for row in fn])  # (a, b, [k, j, i])
+            # the coordinate that is constant (0 or N) over the face in e2, and the step inward
+            for ax in range(3):
+                v = pos[..., ax]
+                if np.all(v == v.flat[0]) and v.flat[0] in (0, N):
+                    break
+            else:
+                raise ValueError("non-conforming face")
+            pos2 = pos.copy()
+            pos2[..., ax] = 1 if pos[0, 0, ax] == 0 else N - 1
+            layer[e, f] = node[e2][pos2[..., 0], pos2[..., 1], pos2[..., 2]]
+    L = element_lengths(level)
+    fdm = {}
+    for e in range(E):
+        for d in range(3):
+            key = (int(btype[e, 2 * d]), int(btype[e, 2 * d + 1]))
+            if key not in fdm:
+                fdm[key] = fdm_1d(N, *key)
+    sch = Schwarz(layer, btype, L, np.zeros(level.n_G), fdm)
+    c = schwarz_sum(level, sch, lambda e, box: box, np.ones(level.n_G))
+    sch.W = np.where(level.free & (c > 0), 1.0 / np.maximum(c, 1.0), 0.0)
+    return sch
+
+
+def box_face_slots(N: int, f: int, a=None):
+    """Index tuple (k, j, i) into an (N+3)^3 box of the face-layer slots of face f."""
+    d, side = divmod(f, 2)
+    c = 0 if side == 0 else N + 2
+    inner = slice(1, N + 2)
+    ijk = [inner, inner, inner]
+    ijk[d] = c
+    return (ijk[2], ijk[1], ijk[0])
+
+
+def schwarz_sum(level: "Level", sch: Schwarz, local, r):
+    """sum_e P_e^T local(e, P_e r): P_e r is the (N+3)^3 box of element e holding r
+    at its own nodes and at its face-layer nodes (zero elsewhere: absent layers
+    and the box's edge and corner strips); P_e^T adds the own and face-layer
+    slots of a box back to their nodes."""
+    N, E = level.N, level.E
+    NP = N + 1
+    node = level.node.reshape(E, NP, NP, NP)
+    z = np.zeros(level.n_G)
+    for e in range(E):
+        box = np.zeros((NP + 2,) * 3)
+        box[1:-1, 1:-1, 1:-1] = r[node[e]]
+        for f in range(6):
+            if sch.btype[e, f] == SCH_NB:
+                # face positions (a, b) run over the two other indices in r, s, t order; the box
+                # slice of face f keeps its remaining axes in (k, j, i) order, i.e. (b, a)
+                box[box_face_slots(N, f)] = r[sch.layer[e, f]].T
+        out = local(e, box)
+        np.add.at(z, node[e], out[1:-1, 1:-1, 1:-1])
+        for f in range(6):
+            if sch.btype[e, f] == SCH_NB:
+                np.add.at(z, sch.layer[e, f].T, out[box_face_slots(N, f)])
+    return z
+
+
+def fdm_solve(sch: Schwarz, e: int, box, h1: float, h2: float):
+    """Fast-diagonalisation solve on the extended box of element e:
+    (S_t x S_s x S_r) diag(1 / (h1 (lam_r + lam_s + lam_t) + h2)) (S_t x S_s x S_r)^T box,
+    for the separable operator h1 (B B A + B A B + A B B) + h2 (B B B) of a box
+    with the element's lengths; S_d = sqrt(2/L_d) S_ref and lam_d = (2/L_d)^2 lam_ref
+    scale the reference data of fdm_1d to length L_d."""
+    Lr, Ls, Lt = sch.L[e]
+    Sr, lr = sch.fdm[(int(sch.btype[e, 0]), int(sch.btype[e, 1]))]
+    Ss, ls = sch.fdm[(int(sch.btype[e, 2]), int(sch.btype[e, 3]))]
+    St, lt = sch.fdm[(int(sch.btype[e, 4]), int(sch.btype[e, 5]))]
+    u = np.einsum("ma,kjm->kja", Sr, box)             # S_r^T along i
+    u = np.einsum("mb,kma->kba", Ss, u)               # S_s^T along j
+    u = np.einsum("mc,mba->cba", St, u)               # S_t^T along k
+    lam = h1 * ((2.0 / Lt) ** 2 * lt[:, None, None] + (2.0 / Ls) ** 2 * ls[None, :, None]
+                + (2.0 / Lr) ** 2 * lr[None, None, :]) + h2
+    u = np.where(lam != 0.0, u / np.where(lam != 0.0, lam, 1.0), 0.0)
+    u = u * ((2.0 / Lr) * (2.0 / Ls) * (2.0 / Lt))
+    u = np.einsum("cm,mba->cba", St, u)
+    u = np.einsum("bm,kma->kba", Ss, u)
+    u = np.einsum("am,kjm->kja", Sr, u)
+    return u
+
+
+def asm_apply(level: "Level", sch: Schwarz, r, h1: float = 1.0, h2: float = 0.0):
+    """Weighted additive Schwarz: z = W sum_e P_e^T F_e P_e r, F_e the local FDM solve,
+    masked. The weight W makes the preconditioner slightly nonsymmetric (Section 3.4)."""
+    z = schwarz_sum(level, sch, lambda e, box: fdm_solve(sch, e, box, h1, h2), r)
+    return level.mask(sch.W * z)
+
+
+def arnoldi_lmax(apply, minv, v0, steps: int = 10) -> float:
+    """Estimate of the largest eigenvalue of M A by ``steps`` Arnoldi steps (modified
+    Gram-Schmidt) from v0: the largest eigenvalue of the symmetric part (H + H^T)/2
+    of the Hessenberg matrix H = V^T M A V, an upper bound on the real parts of
+    its Ritz values."""
+    V = [v0 / np.linalg.norm(v0)]
+    H = np.zeros((steps + 1, steps))
+    k = steps
+    for j in range(steps):
+        w = minv(apply(V[j]))
+        for i in range(j + 1):
+            H[i, j] = V[i] @ w
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j] == 0.0:
+            k = j + 1
+            break
+        V.append(w / H[j + 1, j])
+    Hk = H[:k, :k]
+    return float(np.max(np.linalg.eigvalsh(0.5 * (Hk + Hk.T))))
+
+
+# ----------------------------------------------------------------------------
 # Krylov solvers, smoother, eigenvalue estimate, V-cycle
 # ----------------------------------------------------------------------------
 
@@ -592,8 +837,12 @@ def cheb_smooth(apply, dinv, b, x, lmin: float, lmax: float, degree: int):
     theta = (lmax+lmin)/2, delta = (lmax-lmin)/2, sigma = theta/delta, rho = 1/sigma;
     d = D^{-1} r / theta, x += d; then for each further step:
     r = b - A x, rho' = 1/(2 sigma - rho), d = rho' rho d + (2 rho'/delta) D^{-1} r, x += d.
-    ``x`` None means a zero initial guess (r = b without a matvec).
+    ``x`` None means a zero initial guess (r = b without a matvec). A callable
+    ``dinv`` replaces D^{-1} r by dinv(r) (Chebyshev-accelerated Schwarz, CHEBY-ASM).
     """
+    if not callable(dinv):
+        dvec = dinv
+        dinv = lambda v: dvec * v
     theta = 0.5 * (lmax + lmin)
     delta = 0.5 * (lmax - lmin)
     sigma = theta / delta
@@ -603,12 +852,12 @@ def cheb_smooth(apply, dinv, b, x, lmin: float, lmax: float, degree: int):
         x = np.zeros_like(b)
     else:
         r = b - apply(x)
-    d = dinv * r / theta
+    d = dinv(r) / theta
     x = x + d
     for _ in range(1, degree):
         r = b - apply(x)
         rho_new = 1.0 / (2.0 * sigma - rho)
-        d = rho_new * rho * d + (2.0 * rho_new / delta) * (dinv * r)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * dinv(r)
         x = x + d
         rho = rho_new
     return x
@@ -673,12 +922,14 @@ class MGParams:
     lanczos_seed: int = 1
     coarse_tol: float = 1e-2
     coarse_maxit: int = 100
-    lmax: list | None = None     # per smoothed level; estimated by Lanczos when None
+    lmax: list | None = None     # per smoothed level; estimated by Lanczos/Arnoldi when None
+    smoother: str = "jacobi"     # "jacobi" (CHEBY-JAC) or "asm" (CHEBY-ASM)
 
 
 class PMG:
-    """p-multigrid V-cycle with Chebyshev-Jacobi smoothing on every level but the
-    coarsest and a Jacobi-PCG coarse solve (Section 3.4, "Poisson Solve Preconditioning")."""
+    """p-multigrid V-cycle with Chebyshev-accelerated smoothing (Jacobi or the
+    overlapping Schwarz smoother) on every level but the coarsest and a
+    Jacobi-PCG coarse solve (Section 3.4, "Poisson Solve Preconditioning")."""
 
     def __init__(self, levels, h1=1.0, h2=0.0, params: MGParams | None = None):
         self.levels = levels
@@ -686,16 +937,28 @@ class PMG:
         self.p = params or MGParams()
         self.dinv = [np.where(L.free, 1.0 / L.diag(h1, h2), 0.0) for L in levels]
         self.ops = [(lambda v, L=L: L.apply(v, h1, h2)) for L in levels]
+        nsm = len(levels) - 1
+        if self.p.smoother == "asm":
+            self.sch = [schwarz_setup(levels[l]) for l in range(nsm)]
+            self.minv = [(lambda r, L=levels[l], S=self.sch[l]: asm_apply(L, S, r, h1, h2)) for l in range(nsm)]
+        elif self.p.smoother == "jacobi":
+            self.minv = [self.dinv[l] for l in range(nsm)]
+        else:
+            raise ValueError(self.p.smoother)
         if self.p.lmax is None:
-            self.lmax = [lanczos_lmax(self.ops[l], self.dinv[l], lanczos_start(levels[l], self.p.lanczos_seed),
-                                      self.p.lanczos_steps) for l in range(len(levels) - 1)]
+            if self.p.smoother == "asm":
+                self.lmax = [arnoldi_lmax(self.ops[l], self.minv[l], lanczos_start(levels[l], self.p.lanczos_seed),
+                                          self.p.lanczos_steps) for l in range(nsm)]
+            else:
+                self.lmax = [lanczos_lmax(self.ops[l], self.dinv[l], lanczos_start(levels[l], self.p.lanczos_seed),
+                                          self.p.lanczos_steps) for l in range(nsm)]
         else:
             self.lmax = list(self.p.lmax)
         self.coarse_iters = []
 
     def smooth(self, l, b, x):
         lam = self.lmax[l]
-        return cheb_smooth(self.ops[l], self.dinv[l], b, x, self.p.lmin_factor * lam,
+        return cheb_smooth(self.ops[l], self.minv[l], b, x, self.p.lmin_factor * lam,
                            self.p.lmax_factor * lam, self.p.degree)
 
     def vcycle(self, l, r):
