@@ -236,19 +236,26 @@ def solve_bench(ctx_cls, args, dev):
     import sem_inputs as si
 
     mesh = si.box_mesh(args.solve_elements, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
-    ctx = ctx_cls.from_mesh(mesh)
+    ctxs = {"jacobi": ctx_cls.from_mesh(mesh)}
+    ctx = ctxs["jacobi"]
     b = torch.tensor(si.gaussian_assembled_rhs(mesh, 0).ravel(), device=dev)
     out = {"workload": f"{args.solve_elements}^3 warped box, N=7, x=0 Dirichlet, Gaussian zero-mean RHS, "
-                       f"FCG + p-MG (7-3-1, Chebyshev-Jacobi degree 2, coarse Jacobi-PCG) to 1e-8",
+                       f"FCG + p-MG (7-3-1, Chebyshev degree 2 with Jacobi or Schwarz (asm_*), "
+                       f"coarse Jacobi-PCG) to 1e-8",
            "n_L": int(mesh["x"].size), "n_G": int(ctx.levels[0]["nG"])}
     stream = torch.cuda.current_stream()
-    variants = (("fp64", "fp64", False), ("fp32", "fp32", False), ("bf16g", "bf16g", False),
-                ("fp32_outer_pairs", "fp32", True))
+    variants = (("fp64", "fp64", False, "jacobi"), ("fp32", "fp32", False, "jacobi"),
+                ("bf16g", "bf16g", False, "jacobi"), ("fp32_outer_pairs", "fp32", True, "jacobi"),
+                ("asm_fp64", "fp64", False, "asm"), ("asm_fp32", "fp32", False, "asm"),
+                ("asm_fp32_outer_pairs", "fp32", True, "asm"))
     if args.solve_variants:
         keep = set(args.solve_variants.split(","))
         variants = tuple(v for v in variants if v[0] in keep)
-    for name, prec, op in variants:
-        solve = lambda: ctx.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled", outer_pairs=op)
+    for name, prec, op, sm in variants:
+        if sm not in ctxs:
+            ctxs[sm] = ctx_cls.from_mesh(mesh, smoother=sm)
+        c = ctxs[sm]
+        solve = lambda: c.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled", outer_pairs=op)
         solve()   # warm-up, includes the preconditioner setup for this precision
         times, info = [], None
         for _ in range(args.solve_reps):
@@ -263,7 +270,8 @@ def solve_bench(ctx_cls, args, dev):
         t = min(times)
         out[name] = {"time_to_1e-8_s": t, "median_s": statistics.median(times), "iters": info["iters"],
                      "ms_per_iter": 1e3 * t / max(1, info["iters"]), "relres": info["relres"],
-                     "coarse_iters": info["coarse_iters"], "smoother": prec, "outer_operator": "f32x2" if op else "f64"}
+                     "coarse_iters": info["coarse_iters"], "smoother": f"cheby-{'asm' if sm == 'asm' else 'jac'} {prec}",
+                     "outer_operator": "f32x2" if op else "f64"}
     if args.jacobi:
         ctx.solve(b, tol=1e-8, maxit=20000, precond="jacobi", rhs="assembled")
         torch.cuda.synchronize()
@@ -273,7 +281,8 @@ def solve_bench(ctx_cls, args, dev):
         t = time.perf_counter() - t0
         out["jacobi_fp64"] = {"time_to_1e-8_s": t, "iters": info["iters"], "ms_per_iter": 1e3 * t / info["iters"],
                               "relres": info["relres"]}
-    ctx.close()
+    for c in ctxs.values():
+        c.close()
     return out
 
 

@@ -66,6 +66,10 @@ extern "C" {
 #define SEM_GS_ADD 0         /* w_L <- QQ^T w_L */
 #define SEM_GS_ADD_MASK 1    /* w_L <- R QQ^T w_L (zero every copy of a Dirichlet node) */
 
+/* multigrid smoothers (sem_opts.smoother), Section 3.4 */
+#define SEM_SMOOTH_JACOBI 0  /* Chebyshev-accelerated Jacobi (CHEBY-JAC) */
+#define SEM_SMOOTH_ASM 1     /* Chebyshev-accelerated overlapping Schwarz with FDM local solves (CHEBY-ASM) */
+
 /* sem_solve preconditioners and flags */
 #define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */
 #define SEM_PC_PMG 1         /* flexible PCG + p-multigrid V-cycle with Chebyshev-Jacobi smoothing */
@@ -106,6 +110,7 @@ typedef struct {
   double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-2) */
   int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
   int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
+  int32_t smoother;          /* SEM_SMOOTH_JACOBI (CHEBY-JAC, default) or SEM_SMOOTH_ASM (CHEBY-ASM) */
 } sem_opts;
 
 /* Coefficients h1 (diffusion) and h2 (mass) of A = D^T h1 G D + h2 B. */
@@ -187,13 +192,31 @@ int sem_level_dinv(sem_ctx* ctx, int level, double h1, double h2, double* dinv_L
 int sem_prolong_add(sem_ctx* ctx, int level, int prec, const void* ec_L, void* xf_L, void* stream);
 int sem_restrict(sem_ctx* ctx, int level, int prec, const void* rf_L, void* rc_L, void* stream);
 
-/* Set up the preconditioner for coefficients (h1, h2): Jacobi diagonals and
- * Lanczos estimates of lambda_max(D^-1 A) on every smoothed level, in the
- * arithmetic `prec` of the V-cycle. Synchronous. */
+/* Set up the preconditioner for coefficients (h1, h2): Jacobi diagonals and,
+ * on every smoothed level, an estimate of lambda_max of the smoothed operator:
+ * the largest Ritz value of Lanczos on D^-1 A (CHEBY-JAC), or for CHEBY-ASM
+ * the largest eigenvalue of the symmetric part of the Arnoldi Hessenberg
+ * matrix of M_ASM A (an upper bound on the real parts of its Ritz values),
+ * lanczos_steps steps from the seeded start vector, in FP64. Synchronous. */
 int sem_precond_setup(sem_ctx* ctx, double h1, double h2, int prec, void* stream);
-/* Chebyshev-Jacobi smoothing on `level` (needs sem_precond_setup): x <- S(b, x);
+/* Chebyshev smoothing (Jacobi or Schwarz, per sem_opts.smoother) on `level` (needs sem_precond_setup): x <- S(b, x);
  * x_is_zero != 0 treats x as 0 on entry. Vectors in the V-cycle's precision. */
 int sem_cheb_smooth(sem_ctx* ctx, int level, const void* b_L, void* x_L, int x_is_zero, void* stream);
+/* Weighted overlapping additive Schwarz on `level` (Section 3.4): z = W sum_e
+ * P_e^T F_e P_e r, masked. P_e gathers r on element e's (N+3)^3 extended box:
+ * its own (N+1)^3 nodes and, across each face with a neighbour, the
+ * neighbour's nodes one step inside from the shared face (the box's edge and
+ * corner strips stay zero); P_e^T adds those slots back. F_e is the fast-
+ * diagonalisation inverse of the separable operator h1 (B x B x A + B x A x B +
+ * A x B x B) + h2 (B x B x B) of a box with the element's mean lengths, built
+ * from the 1-D GLL stiffness A and mass B of the extended segment (the element
+ * and same-length neighbours, Dirichlet one node beyond the overlap; a
+ * Dirichlet boundary side drops its boundary node, a Neumann side keeps it).
+ * W = 1 / (number of subdomain slots holding the node), 0 at Dirichlet nodes.
+ * Needs 2 <= N on the level; the data are built on the first call (synchronous).
+ * prec: SEM_FP64 (double vectors) or SEM_FP32 (float vectors). */
+int sem_asm_apply(sem_ctx* ctx, int level, int prec, const void* r_L, void* z_L, double h1, double h2,
+                  void* stream);
 /* z_L = M r_L: one V-cycle (needs sem_precond_setup), FP64 in and out. */
 int sem_vcycle(sem_ctx* ctx, const double* r_L, double* z_L, void* stream);
 /* Read back the lambda_max estimates (after sem_precond_setup). */

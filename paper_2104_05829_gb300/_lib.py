@@ -25,6 +25,7 @@ SEM_PC_JACOBI, SEM_PC_PMG = 0, 1
 SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN, SEM_OUTER_PAIRS = 0, 1, 2, 4
 SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
+SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
 
 
 class SemMesh(C.Structure):
@@ -38,7 +39,7 @@ class SemOpts(C.Structure):
                 ("cheb_degree", C.c_int32), ("cheb_lmin_factor", C.c_double),
                 ("cheb_lmax_factor", C.c_double), ("lanczos_steps", C.c_int32),
                 ("lanczos_seed", C.c_uint64), ("coarse_tol", C.c_double),
-                ("coarse_maxit", C.c_int32), ("prec_copies", C.c_int32)]
+                ("coarse_maxit", C.c_int32), ("prec_copies", C.c_int32), ("smoother", C.c_int32)]
 
 
 class SemCoef(C.Structure):
@@ -80,6 +81,7 @@ SIGNATURES = {
     "sem_precond_setup": (_I, [_P, _D, _D, _I, _P]),
     "sem_cheb_smooth": (_I, [_P, _I, _P, _P, _I, _P]),
     "sem_vcycle": (_I, [_P, _P, _P, _P]),
+    "sem_asm_apply": (_I, [_P, _I, _I, _P, _P, _D, _D, _P]),
     "sem_get_lmax": (_I, [_P, _P, _I]),
     "sem_solve": (_I, [_P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),
     "sem_solve_proj": (_I, [_P, _P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),

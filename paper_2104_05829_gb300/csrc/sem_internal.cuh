@@ -96,6 +96,22 @@ struct Level {
   float *fb = nullptr, *fx = nullptr, *fr = nullptr, *fd = nullptr, *fw = nullptr;
   double *cp = nullptr;      // extra FP64 vector (coarse PCG direction)
   float *cpf = nullptr;
+  // overlapping Schwarz smoother (asm.cu; built on first use)
+  bool sch_ready = false;
+  int32_t* sch_layer = nullptr;   // [E][6][NP*NP] local index of each face-layer node, -1 without neighbour
+  uint8_t* sch_bt = nullptr;      // [E][6] side types: 0 neighbour, 1 Dirichlet boundary, 2 Neumann boundary
+  double* sch_len = nullptr;      // [E][3] mean element lengths along r, s, t
+  float* sch_len32 = nullptr;
+  double* sch_ref = nullptr;      // [9][(N+3)^2 + (N+3)] reference 1-D eigenvectors and eigenvalues per side pair
+  float* sch_ref32 = nullptr;
+  double* sch_w = nullptr;        // [nL] Schwarz weights 1/count, 0 at Dirichlet nodes
+  float* sch_w32 = nullptr;
+  double* sch_zf = nullptr;       // [E][6][NP*NP] staged face-layer outputs
+  float* sch_zf32 = nullptr;
+  int32_t* sch_pts = nullptr;     // local points that receive face-layer outputs
+  int32_t* sch_poff = nullptr;    // CSR offsets into sch_psrc
+  int32_t* sch_psrc = nullptr;    // staged slots per point, in slot order
+  int64_t sch_npts = 0;
 };
 
 // Device scalar slots (double) used by the Krylov kernels.
@@ -195,6 +211,15 @@ int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, 
 int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, void* d, double c1, double c2,
               cudaStream_t s);
 int residual_weighted(const Level& L, int prec, const void* b, const void* w, void* out, cudaStream_t s);
+
+// ---- asm.cu: overlapping Schwarz smoother with fast-diagonalisation local solves
+int schwarz_build(Ctx& C, Level& L, cudaStream_t s);
+int asm_sum(const Level& L, int prec, const void* b, const void* w, void* z, double h1, double h2, cudaStream_t s);
+int asm_weight(const Level& L, int prec, void* z, cudaStream_t s);
+int cheb_w_update(const Level& L, int prec, const void* z, void* x, void* d, double c1, double c2, bool first,
+                  bool x_zero, cudaStream_t s);
+int arnoldi_lmax_asm(Ctx& C, int l, double h1, double h2, const double* v0, int steps, cudaStream_t s,
+                     double* lam);
 
 // ---- proj.cu: projection of successive right-hand sides
 struct Proj;

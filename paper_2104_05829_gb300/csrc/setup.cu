@@ -221,7 +221,9 @@ int dmalloc(T** p, size_t count) {
 void free_level(Level& L) {
   void* ptrs[] = {L.G, L.G32, L.G16, L.G2, L.x, L.y, L.z, L.gid, L.dflag, L.ids, L.off, L.idx, L.mult, L.node,
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
-                  L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf};
+                  L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
+                  L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
+                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -346,6 +348,7 @@ void sem_default_opts(sem_opts* o) {
   o->coarse_tol = 1e-2;
   o->coarse_maxit = 100;
   o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
+  o->smoother = SEM_SMOOTH_JACOBI;
 }
 
 const char* sem_strerror(int code) {
@@ -404,7 +407,8 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   sem_opts o;
   if (opts_in) o = *opts_in;
   else sem_default_opts(&o);
-  if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor)) {
+  if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
+      (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM)) {
     set_detail("invalid smoother / Lanczos / coarse-solve options");
     return SEM_EINVAL;
   }

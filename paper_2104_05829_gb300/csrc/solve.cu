@@ -183,7 +183,31 @@ VecSet vecs(Level& L, int prec) {
   return {L.fb, L.fx, L.fr, L.fd, L.fw, L.cpf, L.dinv32};
 }
 
+// Chebyshev-accelerated weighted Schwarz (CHEBY-ASM): the Chebyshev-Jacobi
+// recurrence with D^-1 r replaced by the Schwarz output W z, z = asm_sum(b - A x);
+// the Schwarz output lives in the level's r vector (unused on smoothed levels).
+int cheb_asm(Ctx& C, int l, int prec, const void* b, void* x, bool x_zero, cudaStream_t s) {
+  Level& L = C.lev[l];
+  VecSet v = vecs(L, prec);
+  const double lmin = C.opts.cheb_lmin_factor * L.lmax, lmax = C.opts.cheb_lmax_factor * L.lmax;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (!x_zero) SEM_TRY(level_op(C, l, prec, x, v.w, C.pc_h1, C.pc_h2, s));
+  SEM_TRY(asm_sum(L, prec, b, x_zero ? nullptr : v.w, v.r, C.pc_h1, C.pc_h2, s));
+  SEM_TRY(cheb_w_update(L, prec, v.r, x, v.d, 0.0, 1.0 / theta, true, x_zero, s));
+  for (int j = 1; j < C.opts.cheb_degree; ++j) {
+    SEM_TRY(level_op(C, l, prec, x, v.w, C.pc_h1, C.pc_h2, s));
+    SEM_TRY(asm_sum(L, prec, b, v.w, v.r, C.pc_h1, C.pc_h2, s));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    SEM_TRY(cheb_w_update(L, prec, v.r, x, v.d, rho_new * rho, 2.0 * rho_new / delta, false, false, s));
+    rho = rho_new;
+  }
+  return SEM_OK;
+}
+
 int cheb(Ctx& C, int l, int prec, const void* b, void* x, bool x_zero, cudaStream_t s) {
+  if (C.opts.smoother == SEM_SMOOTH_ASM) return cheb_asm(C, l, prec, b, x, x_zero, s);
   Level& L = C.lev[l];
   VecSet v = vecs(L, prec);
   const double lmin = C.opts.cheb_lmin_factor * L.lmax, lmax = C.opts.cheb_lmax_factor * L.lmax;
@@ -280,7 +304,15 @@ int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
   for (int l = 0; l < C.nlevels; ++l) {
     Level& L = C.lev[l];
     SEM_TRY(level_dinv(C, l, h1, h2, nullptr, L.dinv, L.dinv32, s));
-    if (l < C.nlevels - 1) SEM_TRY(lanczos(C, l, h1, h2, s, &L.lmax));
+    if (l == C.nlevels - 1) continue;
+    if (C.opts.smoother == SEM_SMOOTH_ASM) {
+      SEM_TRY(schwarz_build(C, L, s));
+      k_lanczos_start<<<vgrid(L.nL), 256, 0, s>>>(L.nL, L.label, L.dmask, C.opts.lanczos_seed, L.vb);
+      SEM_LAUNCH_CHECK();
+      SEM_TRY(arnoldi_lmax_asm(C, l, h1, h2, L.vb, C.opts.lanczos_steps, s, &L.lmax));
+    } else {
+      SEM_TRY(lanczos(C, l, h1, h2, s, &L.lmax));
+    }
   }
   SEM_CUDA_TRY(cudaStreamSynchronize(s));
   C.pc_h1 = h1;
@@ -431,6 +463,24 @@ int sem_cheb_smooth(sem_ctx* h, int level, const void* b, void* x, int x_is_zero
     return SEM_EINVAL;
   }
   return cheb(*C, level, C->pc_prec, b, x, x_is_zero != 0, (cudaStream_t)stream);
+}
+
+int sem_asm_apply(sem_ctx* h, int level, int prec, const void* r, void* z, double h1, double h2, void* stream) {
+  Ctx* C = ctx_of(h);
+  SEM_TRY(check_level(C, level));
+  if (!r || !z || r == z || (prec != SEM_FP64 && prec != SEM_FP32)) {
+    set_detail("sem_asm_apply: NULL or aliased vector, or precision other than SEM_FP64/SEM_FP32");
+    return SEM_EINVAL;
+  }
+  Level& L = C->lev[level];
+  if (prec == SEM_FP32 && !L.G32 && !L.G16) {
+    set_detail("sem_asm_apply: FP32 copies were not built");
+    return SEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SEM_TRY(schwarz_build(*C, L, s));
+  SEM_TRY(asm_sum(L, prec, r, nullptr, z, h1, h2, s));
+  return asm_weight(L, prec, z, s);
 }
 
 int sem_vcycle(sem_ctx* h, const double* r, double* z, void* stream) {

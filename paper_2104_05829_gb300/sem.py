@@ -48,6 +48,8 @@ def default_opts(**kw) -> L.SemOpts:
             o.mg_nlevels = len(v)
             for i, n in enumerate(v):
                 o.mg_orders[i] = int(n)
+        elif k == "smoother":
+            o.smoother = {"jacobi": L.SEM_SMOOTH_JACOBI, "asm": L.SEM_SMOOTH_ASM}.get(v, v)
         elif not hasattr(o, k):
             raise KeyError(k)
         else:
@@ -204,6 +206,14 @@ class SemContext:
                                           self._vec(x, level, prec, "x"), 1 if x_is_zero else 0, _stream(stream)),
                 "sem_cheb_smooth")
         return x
+
+    def asm_apply(self, level, r, z=None, h1=1.0, h2=0.0, prec="fp64", stream=None):
+        """Weighted overlapping Schwarz z = W sum_e P_e^T F_e P_e r on `level` (sem_asm_apply)."""
+        z = torch.empty_like(r) if z is None else z
+        L.check(self._lib.sem_asm_apply(self._h, level, _PREC[prec], self._vec(r, level, prec, "r"),
+                                        self._vec(z, level, prec, "z"), float(h1), float(h2), _stream(stream)),
+                "sem_asm_apply")
+        return z
 
     def vcycle(self, r, z=None, stream=None):
         z = torch.empty_like(r) if z is None else z
