@@ -236,7 +236,8 @@ def solve_bench(ctx_cls, args, dev):
     import sem_inputs as si
 
     mesh = si.box_mesh(args.solve_elements, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
-    ctxs = {"jacobi": ctx_cls.from_mesh(mesh)}
+    copts = {"coarse_mode": args.coarse_mode}
+    ctxs = {"jacobi": ctx_cls.from_mesh(mesh, **copts)}
     ctx = ctxs["jacobi"]
     b = torch.tensor(si.gaussian_assembled_rhs(mesh, 0).ravel(), device=dev)
     out = {"workload": f"{args.solve_elements}^3 warped box, N=7, x=0 Dirichlet, Gaussian zero-mean RHS, "
@@ -253,7 +254,7 @@ def solve_bench(ctx_cls, args, dev):
         variants = tuple(v for v in variants if v[0] in keep)
     for name, prec, op, sm in variants:
         if sm not in ctxs:
-            ctxs[sm] = ctx_cls.from_mesh(mesh, smoother=sm)
+            ctxs[sm] = ctx_cls.from_mesh(mesh, smoother=sm, **copts)
         c = ctxs[sm]
         solve = lambda: c.solve(b, tol=1e-8, maxit=300, precond="pmg", prec=prec, rhs="assembled", outer_pairs=op)
         solve()   # warm-up, includes the preconditioner setup for this precision
@@ -380,6 +381,8 @@ def main():
     ap.add_argument("--solve-48", action="store_true", help="also time the 48^3-element (56.6M-point) solve")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-proj", action="store_true", help="skip the successive-RHS projection sequence")
+    ap.add_argument("--coarse-mode", default="auto", choices=["auto", "cluster", "kernels"],
+                    help="execution of the coarse Jacobi-PCG (same algorithm)")
     ap.add_argument("--proj-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -70,6 +70,11 @@ extern "C" {
 #define SEM_SMOOTH_JACOBI 0  /* Chebyshev-accelerated Jacobi (CHEBY-JAC) */
 #define SEM_SMOOTH_ASM 1     /* Chebyshev-accelerated overlapping Schwarz with FDM local solves (CHEBY-ASM) */
 
+/* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in all three */
+#define SEM_COARSE_AUTO 0     /* one cooperative launch over the whole GPU when it fits, else as below */
+#define SEM_COARSE_CLUSTER 1  /* one launch on one thread-block cluster (FP32/BF16 V-cycles), else kernels */
+#define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches */
+
 /* sem_solve preconditioners and flags */
 #define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */
 #define SEM_PC_PMG 1         /* flexible PCG + p-multigrid V-cycle with Chebyshev-Jacobi smoothing */
@@ -111,6 +116,7 @@ typedef struct {
   int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
   int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
   int32_t smoother;          /* SEM_SMOOTH_JACOBI (CHEBY-JAC, default) or SEM_SMOOTH_ASM (CHEBY-ASM) */
+  int32_t coarse_mode;       /* how the order-1 coarse Jacobi-PCG runs: SEM_COARSE_* (default AUTO) */
 } sem_opts;
 
 /* Coefficients h1 (diffusion) and h2 (mass) of A = D^T h1 G D + h2 B. */

@@ -26,6 +26,7 @@ SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN, SEM_OUTER_PAIRS = 0, 1, 2, 4
 SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
+SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS = 0, 1, 2
 
 
 class SemMesh(C.Structure):
@@ -39,7 +40,8 @@ class SemOpts(C.Structure):
                 ("cheb_degree", C.c_int32), ("cheb_lmin_factor", C.c_double),
                 ("cheb_lmax_factor", C.c_double), ("lanczos_steps", C.c_int32),
                 ("lanczos_seed", C.c_uint64), ("coarse_tol", C.c_double),
-                ("coarse_maxit", C.c_int32), ("prec_copies", C.c_int32), ("smoother", C.c_int32)]
+                ("coarse_maxit", C.c_int32), ("prec_copies", C.c_int32), ("smoother", C.c_int32),
+                ("coarse_mode", C.c_int32)]
 
 
 class SemCoef(C.Structure):

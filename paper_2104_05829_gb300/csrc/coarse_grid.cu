@@ -1,0 +1,401 @@
+// Coarsest-level Jacobi-PCG (order 1) in one cooperative launch over the whole GPU.
+//
+// The coarse problem (a few hundred thousand local points) is latency-bound:
+// a kernel per Krylov step pays launch gaps, and a single cluster has too few
+// SMs. Here every SM takes a slice of whole elements; per-point Krylov vectors
+// (x, r, p, the Jacobi weights and flags) live in registers for the whole
+// solve, each block's geometric factors are staged once in shared memory, and
+// phases are separated by a grid barrier. An iteration has three barriers:
+//   1. element operator w_L = A_L p (registers + shared memory, warp shuffles), then barrier;
+//   2. gather-scatter of the shared nodes (segments split across blocks) with
+//      the (p, w) products of their owner copies, then barrier;
+//   3. alpha from the reduced (p, w); x += alpha p, r -= alpha w; (r, r) and
+//      (r, D^-1 r), then barrier; beta, convergence; p = D^-1 r + beta p.
+// Sums: per-thread partials (FP32 in the FP32 solve), block sums in FP64
+// written to a partial array; after the barrier every block adds all block
+// partials in the same fixed order, so all blocks hold the same bits and take
+// the same branches. The barrier is a generation counter with bounded waiting:
+// a block that waits longer than about a second sets an error flag, after
+// which every barrier returns at once and the solve reports a breakdown.
+// The algorithm is the multi-kernel one: x0 = 0, r = b, z = D^-1 r, stop when
+// (r, r) <= tol^2 (b, b) or after maxit iterations.
+#include <algorithm>
+
+#include "sem_internal.cuh"
+
+namespace sem {
+
+namespace {
+
+constexpr int GT_THREADS = 256;
+constexpr int NPC = 2;              // order 1
+constexpr int NPC3 = 8;
+
+struct GridArgs {
+  int E;
+  int64_t nseg;
+  const void* G;                    // [E][7][8]
+  const void* b;
+  void* x;
+  void* p_glob;                     // p at every point, read by the gather-scatter phase
+  void* w;
+  const void* dinv;
+  const uint8_t* own;
+  const int32_t* mult;
+  const int32_t* seg_off;
+  const int32_t* seg_idx;
+  const uint8_t* seg_dir;
+  double h1, h2;
+  double tol;
+  int maxit;
+  int epb;                          // elements per block
+  double* part;                     // [3][gridDim.x] block partials
+  unsigned* bar;                    // [0] arrival count, [1] generation
+  int* err;                         // barrier timeout flag
+  double* sc;                       // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
+};
+
+// factor value in the arithmetic type (FP64 factors stay FP64)
+__device__ __forceinline__ double fval(double v) { return v; }
+__device__ __forceinline__ float fval(float v) { return v; }
+__device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Grid barrier with bounded waiting (generation counter).
+__device__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    if (*(volatile int*)err == 0) {
+      const unsigned g = *gen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicExch(bar + 1, g + 1);
+      } else {
+        unsigned spins = 0;
+        while (*gen == g) {
+          if (*(volatile int*)err != 0) break;   // another block gave up: stop waiting
+          __nanosleep(64);
+          if (++spins > (1u << 24)) {   // about a second
+            atomicExch(err, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+  }
+  __syncthreads();
+}
+
+// Block sum of NS values into part[s * nblk + blockIdx.x] (FP64), lane 0 of warp 0 writes.
+template <int NS, typename T>
+__device__ void block_partial(T (&v)[NS], double* part) {
+  __shared__ double s_w[GT_THREADS / 32][NS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_xor_sync(0xffffffffu, v[s], o);
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_w[warp][s] = (double)v[s];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (int q = 0; q < GT_THREADS / 32; ++q) t += s_w[q][s];
+      __stcg(part + s * gridDim.x + blockIdx.x, t);
+    }
+}
+
+// Totals of the block partials, identical in every block (warp 0 reads them all
+// in a fixed lane-strided order and reduces in a fixed shuffle tree).
+template <int NS>
+__device__ void grid_totals(const double* part, double* tot) {
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double t = 0;
+      for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) t += __ldcg(part + s * gridDim.x + q);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) tot[s] = t;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, typename GT, int PPT, bool SMEM_G>
+__global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  GT* sG = reinterpret_cast<GT*>(s_raw);
+  __shared__ double tot[2];
+  __shared__ int s_flag;
+  const T* b = static_cast<const T*>(a.b);
+  T* xg = static_cast<T*>(a.x);
+  T* pg = static_cast<T*>(a.p_glob);
+  T* w = static_cast<T*>(a.w);
+  const T* dv = static_cast<const T*>(a.dinv);
+  const GT* G = static_cast<const GT*>(a.G);
+  const int e0 = min(a.E, (int)blockIdx.x * a.epb), e1 = min(a.E, e0 + a.epb);
+  const int64_t p0 = (int64_t)e0 * NPC3;
+  const int npts = (e1 - e0) * NPC3;
+  // stage this block's factors (or read them from global memory when they do not fit)
+  if (SMEM_G)
+    for (int q = threadIdx.x; q < (e1 - e0) * 7 * NPC3; q += GT_THREADS) sG[q] = G[(int64_t)e0 * 7 * NPC3 + q];
+  const GT* gb = SMEM_G ? sG : G + (int64_t)e0 * 7 * NPC3;
+  // per-thread points: c-th point is p0 + threadIdx.x + c * GT_THREADS
+  const int lq = threadIdx.x & 7;
+  const int i = lq & 1, j = (lq >> 1) & 1, k = lq >> 2;
+  const T d00 = (T)D.a[0], d01 = (T)D.a[1], d10 = (T)D.a[2], d11 = (T)D.a[3];
+  const T di_s = i ? d11 : d00, di_o = i ? d10 : d01;
+  const T dj_s = j ? d11 : d00, dj_o = j ? d10 : d01;
+  const T dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
+  const T ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;
+  const T h1 = (T)a.h1, h2 = (T)a.h2;
+  T x[PPT], r[PPT], p[PPT], dinv[PPT];
+  unsigned solo = 0, own = 0, live = 0;   // bit c: point c is an owner / an owner of a one-copy node / exists
+  T acc2[2] = {T(0), T(0)};
+#pragma unroll
+  for (int c = 0; c < PPT; ++c) {
+    const int lp = threadIdx.x + c * GT_THREADS;
+    x[c] = r[c] = p[c] = dinv[c] = T(0);
+    if (lp < npts) {
+      const int64_t l = p0 + lp;
+      live |= 1u << c;
+      const T bl = b[l];
+      dinv[c] = dv[l];
+      r[c] = bl;
+      p[c] = dinv[c] * bl;
+      __stcg(pg + l, p[c]);
+      if (a.own[l]) {
+        own |= 1u << c;
+        if (a.mult[l] == 1) solo |= 1u << c;
+        acc2[0] = fma(bl, bl, acc2[0]);
+        acc2[1] = fma(bl, p[c], acc2[1]);
+      }
+    }
+  }
+  double* partA = a.part;                        // (p, w)
+  double* partB = a.part + gridDim.x;            // (r, r), (r, z): 2 * gridDim.x
+  block_partial<2>(acc2, partB);
+  grid_barrier(a.bar, a.err);
+  grid_totals<2>(partB, tot);
+  // scalars (identical in every block)
+  double bb = tot[0], rz = tot[1], rr = bb;
+  const double tol2 = a.tol * a.tol * bb;
+  int flag = rr <= tol2 ? 1 : 0;   // 0 go on, 1 converged, 2 breakdown
+  int it = 0;
+  const int64_t s0 = a.nseg * blockIdx.x / gridDim.x, s1 = a.nseg * (blockIdx.x + 1) / gridDim.x;
+  while (flag == 0 && it < a.maxit) {
+    // 1. element operator w = A_L p on this block's elements
+    T acc1[1] = {T(0)};
+#pragma unroll
+    for (int c = 0; c < PPT; ++c) {
+      const int lp = threadIdx.x + c * GT_THREADS;
+      if (c * GT_THREADS >= npts) break;          // uniform across the block
+      const bool lv = (live >> c) & 1u;
+      const T u = p[c];
+      const T ur = di_s * u + di_o * __shfl_xor_sync(0xffffffffu, u, 1);
+      const T us = dj_s * u + dj_o * __shfl_xor_sync(0xffffffffu, u, 2);
+      const T ut = dk_s * u + dk_o * __shfl_xor_sync(0xffffffffu, u, 4);
+      T wr = T(0), ws = T(0), wt = T(0), bu = T(0);
+      if (lv) {
+        const int le = lp >> 3;
+        const GT* g = gb + le * 7 * NPC3 + lq;
+        const T g11 = (T)fval(g[0]), g12 = (T)fval(g[8]), g13 = (T)fval(g[16]);
+        const T g22 = (T)fval(g[24]), g23 = (T)fval(g[32]), g33 = (T)fval(g[40]);
+        wr = h1 * (g11 * ur + g12 * us + g13 * ut);
+        ws = h1 * (g12 * ur + g22 * us + g23 * ut);
+        wt = h1 * (g13 * ur + g23 * us + g33 * ut);
+        bu = h2 * (T)fval(g[48]) * u;
+      }
+      T wv = bu + di_s * wr + ti_o * __shfl_xor_sync(0xffffffffu, wr, 1);
+      wv += dj_s * ws + tj_o * __shfl_xor_sync(0xffffffffu, ws, 2);
+      wv += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
+      if (lv) {
+        __stcg(w + p0 + lp, wv);
+        if ((solo >> c) & 1u) acc1[0] = fma(u, wv, acc1[0]);
+      }
+    }
+    grid_barrier(a.bar, a.err);
+    // 2. gather-scatter of shared / Dirichlet nodes, with (p, w) at their owner copies
+    for (int64_t sg = s0 + threadIdx.x; sg < s1; sg += GT_THREADS) {
+      const int bgn = a.seg_off[sg], end = a.seg_off[sg + 1];
+      if (a.seg_dir[sg]) {
+        for (int q = bgn; q < end; ++q) __stcg(w + a.seg_idx[q], T(0));
+      } else {
+        T sum = __ldcg(w + a.seg_idx[bgn]);
+        for (int q = bgn + 1; q < end; ++q) sum += __ldcg(w + a.seg_idx[q]);
+        if (end - bgn > 1)
+          for (int q = bgn; q < end; ++q) __stcg(w + a.seg_idx[q], sum);
+        acc1[0] = fma(__ldcg(pg + a.seg_idx[bgn]), sum, acc1[0]);
+      }
+    }
+    block_partial<1>(acc1, partA);
+    grid_barrier(a.bar, a.err);
+    grid_totals<1>(partA, tot);
+    const double pw = tot[0];
+    if (*(volatile int*)a.err != 0 || !(pw > 0.0) || !isfinite(pw)) {
+      flag = 2;
+      break;
+    }
+    const T alpha = (T)(rz / pw);
+    // 3. x += alpha p, r -= alpha w; (r, r), (r, D^-1 r)
+    T acc3[2] = {T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < PPT; ++c) {
+      if (!((live >> c) & 1u)) continue;
+      const int64_t l = p0 + threadIdx.x + c * GT_THREADS;
+      x[c] = fma(alpha, p[c], x[c]);
+      r[c] = fma(-alpha, __ldcg(w + l), r[c]);
+      if ((own >> c) & 1u) {
+        acc3[0] = fma(r[c], r[c], acc3[0]);
+        acc3[1] = fma(r[c], dinv[c] * r[c], acc3[1]);
+      }
+    }
+    block_partial<2>(acc3, partB);
+    grid_barrier(a.bar, a.err);
+    grid_totals<2>(partB, tot);
+    ++it;
+    rr = tot[0];
+    const double beta = tot[1] / rz;
+    rz = tot[1];
+    if (*(volatile int*)a.err != 0 || !isfinite(rr)) {
+      flag = 2;
+      break;
+    }
+    if (rr <= tol2) {
+      flag = 1;
+      break;
+    }
+    const T bt = (T)beta;
+#pragma unroll
+    for (int c = 0; c < PPT; ++c) {
+      if (!((live >> c) & 1u)) continue;
+      p[c] = fma(bt, p[c], dinv[c] * r[c]);
+      __stcg(pg + p0 + threadIdx.x + c * GT_THREADS, p[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < PPT; ++c)
+    if ((live >> c) & 1u) xg[p0 + threadIdx.x + c * GT_THREADS] = x[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sc[S_ITER] = it;
+    a.sc[S_TOTAL] += it;
+    a.sc[S_RR] = rr;
+    a.sc[S_BB] = bb;
+    a.sc[S_BREAK] = flag == 2 ? 1 : 0;
+    a.sc[S_DONE] = 1;
+  }
+  (void)s_flag;
+}
+
+struct GridPlan {
+  int grid = 0, epb = 0;
+  size_t smem = 0;
+  const void* f = nullptr;
+};
+
+// A plan for PPT points per thread: the grid it needs must be co-resident and at
+// most two blocks per SM (fewer arrivals per barrier).
+template <typename T, typename GT, int PPT, bool SMEM_G>
+bool plan_for(int E, int nsm, GridPlan* out) {
+  const int epb = (PPT * GT_THREADS) / NPC3;                 // elements one block can hold
+  const int grid = (E + epb - 1) / epb;
+  const size_t smem = SMEM_G ? (size_t)epb * 7 * NPC3 * sizeof(GT) : 0;
+  if (smem > 200 * 1024) return false;
+  const void* f = (const void*)k_coarse_grid<T, GT, PPT, SMEM_G>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, GT_THREADS, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (per_sm < 1 || grid > std::min(per_sm, 2) * nsm) return false;
+  out->grid = grid;
+  out->epb = (E + grid - 1) / grid;                          // spread the elements evenly
+  out->smem = SMEM_G ? (size_t)out->epb * 7 * NPC3 * sizeof(GT) : 0;
+  out->f = f;
+  return true;
+}
+
+template <typename T, typename GT>
+bool make_plan(int E, int nsm, GridPlan* pl) {
+  if (plan_for<T, GT, 1, true>(E, nsm, pl) || plan_for<T, GT, 2, true>(E, nsm, pl) ||
+      plan_for<T, GT, 4, true>(E, nsm, pl) || plan_for<T, GT, 8, true>(E, nsm, pl) ||
+      plan_for<T, GT, 16, true>(E, nsm, pl) || plan_for<T, GT, 8, false>(E, nsm, pl) ||
+      plan_for<T, GT, 16, false>(E, nsm, pl))
+    return true;
+  if constexpr (sizeof(T) == 4) return plan_for<T, GT, 32, false>(E, nsm, pl);   // FP64 would spill
+  return false;
+}
+
+template <typename T, typename GT>
+int launch_grid(const Level& L, const GT* G, const void* b, void* x, void* pglob, void* w, const void* dinv,
+                double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
+                cudaStream_t s, bool* used) {
+  *used = false;
+  int dev = 0, nsm = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  GridPlan pl;
+  if (!make_plan<T, GT>(L.E, nsm, &pl)) return SEM_OK;   // does not fit: the caller falls back
+  if (pl.grid > COARSE_GRID_MAX) return SEM_OK;
+  GridArgs a{};
+  a.E = L.E;
+  a.nseg = L.n_seg;
+  a.G = G;
+  a.b = b;
+  a.x = x;
+  a.p_glob = pglob;
+  a.w = w;
+  a.dinv = dinv;
+  a.own = L.owner;
+  a.mult = L.mult;
+  a.seg_off = L.seg_off;
+  a.seg_idx = L.seg_idx;
+  a.seg_dir = L.seg_dir;
+  a.h1 = h1;
+  a.h2 = h2;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.epb = pl.epb;
+  a.part = part;
+  a.bar = bar;
+  a.err = err;
+  a.sc = sc;
+  Mat64 D = L.D;
+  void* args[] = {&a, &D};
+  SEM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+  SEM_CUDA_TRY(cudaLaunchCooperativeKernel(pl.f, dim3(pl.grid), dim3(GT_THREADS), args, pl.smem, s));
+  *used = true;
+  return SEM_OK;
+}
+
+}  // namespace
+
+// Whole-GPU coarse solve at order 1 (FP64, FP32 or BF16-factor V-cycles);
+// *used = false when it does not apply (another order, or the grid does not fit).
+// Scratch: part [3 * grid] doubles, bar [2] unsigned, err [1] int (Level-owned).
+int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p, void* w, const void* dinv,
+                      double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
+                      cudaStream_t s, bool* used) {
+  *used = false;
+  if (L.NP != NPC) return SEM_OK;
+  if (prec == SEM_FP64)
+    return launch_grid<double, double>(L, L.G, b, x, p, w, dinv, h1, h2, tol, maxit, sc, part, bar, err, s, used);
+  if (prec == SEM_FP32)
+    return launch_grid<float, float>(L, L.G32, b, x, p, w, dinv, h1, h2, tol, maxit, sc, part, bar, err, s, used);
+  return launch_grid<float, __nv_bfloat16>(L, L.G16, b, x, p, w, dinv, h1, h2, tol, maxit, sc, part, bar, err, s,
+                                           used);
+}
+
+}  // namespace sem

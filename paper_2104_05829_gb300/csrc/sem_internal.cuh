@@ -151,6 +151,10 @@ struct Ctx {
   cudaEvent_t ev = nullptr;
   cudaEvent_t cev[2] = {nullptr, nullptr};   // coarse-solve batch markers
   double* h_done = nullptr;                  // pinned, 2 slots
+  // scratch of the whole-GPU coarse solve
+  double* cg_part = nullptr;                 // [3 * COARSE_GRID_MAX]
+  unsigned* cg_bar = nullptr;                // [2]
+  int* cg_err = nullptr;                     // [1]
 };
 
 constexpr int RED_BLOCKS = 304;   // 2 per SM on a 152-SM GB300; fixed for determinism
@@ -175,6 +179,12 @@ int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double
 int coarse_cluster_solve(const Level& L, int prec, const void* b, void* x, void* r, void* p, void* w,
                          const void* dinv, double h1, double h2, double tol, int maxit, double* sc,
                          cudaStream_t s, bool* used);
+
+// ---- coarse_grid.cu: one-launch coarse Jacobi-PCG over the whole GPU (cooperative launch)
+constexpr int COARSE_GRID_MAX = 2048;   // largest grid; scratch: part[3 * COARSE_GRID_MAX], bar[2], err[1]
+int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p, void* w, const void* dinv,
+                      double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
+                      cudaStream_t s, bool* used);
 
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);

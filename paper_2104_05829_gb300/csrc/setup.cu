@@ -349,6 +349,7 @@ void sem_default_opts(sem_opts* o) {
   o->coarse_maxit = 100;
   o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
   o->smoother = SEM_SMOOTH_JACOBI;
+  o->coarse_mode = SEM_COARSE_AUTO;
 }
 
 const char* sem_strerror(int code) {
@@ -370,7 +371,8 @@ void sem_free(sem_ctx* h) {
   Ctx* C = reinterpret_cast<Ctx*>(h);
   if (!C) return;
   for (int l = 0; l < SEM_MAX_LEVELS; ++l) free_level(C->lev[l]);
-  void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->dr, C->t};
+  void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->dr, C->t,
+                  C->cg_part, C->cg_bar, C->cg_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (C->h_scal) cudaFreeHost(C->h_scal);
@@ -408,7 +410,8 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   if (opts_in) o = *opts_in;
   else sem_default_opts(&o);
   if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
-      (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM)) {
+      (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM) || o.coarse_mode < SEM_COARSE_AUTO ||
+      o.coarse_mode > SEM_COARSE_KERNELS) {
     set_detail("invalid smoother / Lanczos / coarse-solve options");
     return SEM_EINVAL;
   }
@@ -483,6 +486,9 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   // reduction scratch and fine-level solver workspace
   STEP(dmalloc(&C->red_part, RED_BLOCKS * 4));
   STEP(dmalloc(&C->red_ticket, 1));
+  STEP(dmalloc(&C->cg_part, 3 * COARSE_GRID_MAX));
+  STEP(dmalloc(&C->cg_bar, 2));
+  STEP(dmalloc(&C->cg_err, 1));
   CUSTEP(cudaMemsetAsync(C->red_ticket, 0, sizeof(unsigned), s));
   STEP(dmalloc(&C->scal, 4 * S_NSLOTS));
   CUSTEP(cudaMemsetAsync(C->scal, 0, 4 * S_NSLOTS * sizeof(double), s));

@@ -235,10 +235,16 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   Level& L = C.lev[l];
   VecSet v = vecs(L, prec);
   double* sc = C.scal + 1 * S_NSLOTS;
-  // FP32 / BF16-factor V-cycles at order 1: the whole solve in one cluster launch
+  // order 1: the whole solve in one cooperative launch over the GPU, or (FP32 /
+  // BF16-factor V-cycles) in one launch on one thread-block cluster
   bool used = false;
-  SEM_TRY(coarse_cluster_solve(L, prec, b, x, v.r, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
-                               C.opts.coarse_maxit, sc, s, &used));
+  if (C.opts.coarse_mode == SEM_COARSE_AUTO)
+    SEM_TRY(coarse_grid_solve(L, prec, b, x, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
+                              C.opts.coarse_maxit, sc, C.cg_part, C.cg_bar, C.cg_err, s, &used));
+  if (used) return SEM_OK;
+  if (C.opts.coarse_mode != SEM_COARSE_KERNELS)
+    SEM_TRY(coarse_cluster_solve(L, prec, b, x, v.r, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
+                                 C.opts.coarse_maxit, sc, s, &used));
   if (used) return SEM_OK;
   SEM_TRY(pcg_begin_tol(C, L, prec, b, nullptr, x, v.r, v.dinv, v.p, sc, C.opts.coarse_tol, s));
   // Iterations go out in batches. After each batch the device's "done" flag is

@@ -50,6 +50,9 @@ def default_opts(**kw) -> L.SemOpts:
                 o.mg_orders[i] = int(n)
         elif k == "smoother":
             o.smoother = {"jacobi": L.SEM_SMOOTH_JACOBI, "asm": L.SEM_SMOOTH_ASM}.get(v, v)
+        elif k == "coarse_mode":
+            o.coarse_mode = {"auto": L.SEM_COARSE_AUTO, "cluster": L.SEM_COARSE_CLUSTER,
+                             "kernels": L.SEM_COARSE_KERNELS}.get(v, v)
         elif not hasattr(o, k):
             raise KeyError(k)
         else:

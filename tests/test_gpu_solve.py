@@ -228,3 +228,38 @@ def test_pmg_solve_48cube_all_precisions_residual_by_oracle():
         print(f"{name}: oracle residual {res:.3e}, difference from the FP64 solve {diff:.3e}")
         assert res < 2e-8, (name, res)
         assert diff < 1e-5, (name, diff)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4), ("bf16g", 1e-4)])
+def test_coarse_solve_executions_agree(prec, tol):
+    """The three executions of the coarse Jacobi-PCG (one cooperative launch over the GPU,
+    one cluster launch, batched kernels) run the same algorithm: one V-cycle with 8 coarse
+    iterations gives the same result up to the rounding of their different summation orders."""
+    dev()
+    mesh = si.box_mesh((4, 3, 3), 7, warp=0.1, perm_seed=6, dirichlet=("x0",))
+    L0 = O.level_from_mesh(mesh)
+    r = L0.mask(np.random.default_rng(5).standard_normal(L0.n_G))
+    zs = {}
+    for mode in ("auto", "cluster", "kernels"):
+        ctx = ctx_for(mesh, mg_orders=[7, 3, 1], coarse_tol=0.0, coarse_maxit=8, coarse_mode=mode)
+        ctx.precond_setup(1.0, 0.0, prec)
+        zs[mode] = H(ctx.vcycle(T(_gL(L0, r))))
+        ctx.close()
+    assert relmax(zs["auto"], zs["kernels"]) < tol
+    assert relmax(zs["cluster"], zs["kernels"]) < tol
+
+
+def test_coarse_grid_solve_on_the_48cube_coarse_level():
+    """At 48^3 elements the coarse level (110,592 order-1 elements) needs 32 points per
+    thread with the factors read from global memory; one FP32 V-cycle from the cooperative
+    solve agrees with the batched-kernel solve to FP32 rounding."""
+    dev()
+    mesh = si.box_mesh(48, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
+    b = T(si.gaussian_assembled_rhs(mesh, 0))
+    zs = {}
+    for mode in ("auto", "kernels"):
+        ctx = ctx_for(mesh, coarse_tol=0.0, coarse_maxit=6, coarse_mode=mode, prec_copies=1)
+        ctx.precond_setup(1.0, 0.0, "fp32")
+        zs[mode] = H(ctx.vcycle(b))
+        ctx.close()
+    assert relmax(zs["auto"], zs["kernels"]) < 1e-4
