@@ -237,6 +237,8 @@ def solve_bench(ctx_cls, args, dev):
 
     mesh = si.box_mesh(args.solve_elements, 7, warp=0.1, perm_seed=0, dirichlet=("x0",))
     copts = {"coarse_mode": args.coarse_mode}
+    if args.coarse_tol is not None:
+        copts["coarse_tol"] = args.coarse_tol
     ctxs = {"jacobi": ctx_cls.from_mesh(mesh, **copts)}
     ctx = ctxs["jacobi"]
     b = torch.tensor(si.gaussian_assembled_rhs(mesh, 0).ravel(), device=dev)
@@ -381,7 +383,8 @@ def main():
     ap.add_argument("--solve-48", action="store_true", help="also time the 48^3-element (56.6M-point) solve")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-proj", action="store_true", help="skip the successive-RHS projection sequence")
-    ap.add_argument("--coarse-mode", default="auto", choices=["auto", "cluster", "kernels"],
+    ap.add_argument("--coarse-tol", type=float, default=None, help="coarse Jacobi-PCG tolerance (default 1e-2)")
+    ap.add_argument("--coarse-mode", default="auto", choices=["auto", "cluster", "grid", "kernels"],
                     help="execution of the coarse Jacobi-PCG (same algorithm)")
     ap.add_argument("--proj-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")

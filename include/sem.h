@@ -70,10 +70,11 @@ extern "C" {
 #define SEM_SMOOTH_JACOBI 0  /* Chebyshev-accelerated Jacobi (CHEBY-JAC) */
 #define SEM_SMOOTH_ASM 1     /* Chebyshev-accelerated overlapping Schwarz with FDM local solves (CHEBY-ASM) */
 
-/* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in all three */
-#define SEM_COARSE_AUTO 0     /* one cooperative launch over the whole GPU when it fits, else as below */
-#define SEM_COARSE_CLUSTER 1  /* one launch on one thread-block cluster (FP32/BF16 V-cycles), else kernels */
+/* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in all of them */
+#define SEM_COARSE_AUTO 0     /* the first that applies of GRID, CLUSTER, KERNELS */
+#define SEM_COARSE_CLUSTER 1  /* FP32/BF16 V-cycles: one launch on one cluster, problem held on chip; else KERNELS */
 #define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches */
+#define SEM_COARSE_GRID 3     /* one cooperative launch over the whole GPU when it fits; else KERNELS */
 
 /* sem_solve preconditioners and flags */
 #define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */
@@ -112,7 +113,7 @@ typedef struct {
   double cheb_lmax_factor;   /* (1.1) */
   int32_t lanczos_steps;     /* Lanczos steps for the eigenvalue estimate of D^-1 A (10) */
   uint64_t lanczos_seed;     /* SplitMix64 seed of the Lanczos start vector (1) */
-  double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-2) */
+  double coarse_tol;         /* relative residual of the coarsest-level Jacobi-PCG (1e-1) */
   int32_t coarse_maxit;      /* iteration cap of the coarse solve (100) */
   int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
   int32_t smoother;          /* SEM_SMOOTH_JACOBI (CHEBY-JAC, default) or SEM_SMOOTH_ASM (CHEBY-ASM) */

@@ -920,7 +920,7 @@ class MGParams:
     lmax_factor: float = 1.1
     lanczos_steps: int = 10
     lanczos_seed: int = 1
-    coarse_tol: float = 1e-2
+    coarse_tol: float = 1e-1
     coarse_maxit: int = 100
     lmax: list | None = None     # per smoothed level; estimated by Lanczos/Arnoldi when None
     smoother: str = "jacobi"     # "jacobi" (CHEBY-JAC) or "asm" (CHEBY-ASM)

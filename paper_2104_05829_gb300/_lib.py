@@ -26,7 +26,7 @@ SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN, SEM_OUTER_PAIRS = 0, 1, 2, 4
 SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
-SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS = 0, 1, 2
+SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS, SEM_COARSE_GRID = 0, 1, 2, 3
 
 
 class SemMesh(C.Structure):

@@ -49,6 +49,7 @@ struct GridArgs {
   double tol;
   int maxit;
   int epb;                          // elements per block
+  int spb;                          // gather-scatter segments per block (upper bound, staged in shared memory)
   double* part;                     // [3][gridDim.x] block partials
   unsigned* bar;                    // [0] arrival count, [1] generation
   int* err;                         // barrier timeout flag
@@ -132,8 +133,14 @@ template <typename T, typename GT, int PPT, bool SMEM_G>
 __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   GT* sG = reinterpret_cast<GT*>(s_raw);
+  // after the factors: this block's segments (offsets, copies, Dirichlet flags)
+  const size_t g_bytes = SMEM_G ? ((size_t)a.epb * 7 * NPC3 * sizeof(GT) + 15) / 16 * 16 : 0;
+  int32_t* s_off = reinterpret_cast<int32_t*>(s_raw + g_bytes);    // [spb + 1]
+  int32_t* s_idx = s_off + a.spb + 1;                               // [8 * spb]
+  uint8_t* s_dir = reinterpret_cast<uint8_t*>(s_idx + 8 * a.spb);  // [spb]
   __shared__ double tot[2];
-  __shared__ int s_flag;
+  __shared__ int s_flag;     // 0 go on, 1 converged, 2 breakdown
+  __shared__ T s_scal;       // alpha or beta, computed once per block by thread 0
   const T* b = static_cast<const T*>(a.b);
   T* xg = static_cast<T*>(a.x);
   T* pg = static_cast<T*>(a.p_glob);
@@ -190,13 +197,26 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
   int flag = rr <= tol2 ? 1 : 0;   // 0 go on, 1 converged, 2 breakdown
   int it = 0;
   const int64_t s0 = a.nseg * blockIdx.x / gridDim.x, s1 = a.nseg * (blockIdx.x + 1) / gridDim.x;
+  // stage the block's gather-scatter segments once (they never change); a block whose
+  // segments hold more copies than the staging room reads them from global memory
+  const int ns = (int)(s1 - s0);
+  const int c0 = a.nseg > 0 ? a.seg_off[s0] : 0;
+  const bool staged = ns <= a.spb && a.nseg > 0 && a.seg_off[s1] - c0 <= 8 * a.spb;
+  if (staged) {
+    for (int q = threadIdx.x; q <= ns; q += GT_THREADS) s_off[q] = a.seg_off[s0 + q] - c0;
+    for (int q = threadIdx.x; q < a.seg_off[s1] - c0; q += GT_THREADS) s_idx[q] = a.seg_idx[c0 + q];
+    for (int q = threadIdx.x; q < ns; q += GT_THREADS) s_dir[q] = a.seg_dir[s0 + q];
+  }
+  __syncthreads();
+  const int32_t* g_off = staged ? s_off : a.seg_off + s0;    // offsets relative to g_idx
+  const int32_t* g_idx = staged ? s_idx : a.seg_idx;
+  const uint8_t* g_dir = staged ? s_dir : a.seg_dir + s0;
   while (flag == 0 && it < a.maxit) {
     // 1. element operator w = A_L p on this block's elements
     T acc1[1] = {T(0)};
 #pragma unroll
     for (int c = 0; c < PPT; ++c) {
       const int lp = threadIdx.x + c * GT_THREADS;
-      if (c * GT_THREADS >= npts) break;          // uniform across the block
       const bool lv = (live >> c) & 1u;
       const T u = p[c];
       const T ur = di_s * u + di_o * __shfl_xor_sync(0xffffffffu, u, 1);
@@ -223,27 +243,34 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
     }
     grid_barrier(a.bar, a.err);
     // 2. gather-scatter of shared / Dirichlet nodes, with (p, w) at their owner copies
-    for (int64_t sg = s0 + threadIdx.x; sg < s1; sg += GT_THREADS) {
-      const int bgn = a.seg_off[sg], end = a.seg_off[sg + 1];
-      if (a.seg_dir[sg]) {
-        for (int q = bgn; q < end; ++q) __stcg(w + a.seg_idx[q], T(0));
+    for (int sg = threadIdx.x; sg < ns; sg += GT_THREADS) {
+      const int bgn = g_off[sg], end = g_off[sg + 1];
+      if (g_dir[sg]) {
+        for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], T(0));
       } else {
-        T sum = __ldcg(w + a.seg_idx[bgn]);
-        for (int q = bgn + 1; q < end; ++q) sum += __ldcg(w + a.seg_idx[q]);
+        T sum = __ldcg(w + g_idx[bgn]);
+        for (int q = bgn + 1; q < end; ++q) sum += __ldcg(w + g_idx[q]);
         if (end - bgn > 1)
-          for (int q = bgn; q < end; ++q) __stcg(w + a.seg_idx[q], sum);
-        acc1[0] = fma(__ldcg(pg + a.seg_idx[bgn]), sum, acc1[0]);
+          for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], sum);
+        acc1[0] = fma(__ldcg(pg + g_idx[bgn]), sum, acc1[0]);
       }
     }
     block_partial<1>(acc1, partA);
     grid_barrier(a.bar, a.err);
     grid_totals<1>(partA, tot);
-    const double pw = tot[0];
-    if (*(volatile int*)a.err != 0 || !(pw > 0.0) || !isfinite(pw)) {
+    // the FP64 scalar recurrences run in thread 0 only (FP64 division is slow on this part)
+    if (threadIdx.x == 0) {
+      const double pw = tot[0];
+      const bool bad = *(volatile int*)a.err != 0 || !(pw > 0.0) || !isfinite(pw);
+      s_flag = bad ? 2 : 0;
+      s_scal = bad ? T(0) : (T)(rz / pw);
+    }
+    __syncthreads();
+    if (s_flag != 0) {
       flag = 2;
       break;
     }
-    const T alpha = (T)(rz / pw);
+    const T alpha = s_scal;
     // 3. x += alpha p, r -= alpha w; (r, r), (r, D^-1 r)
     T acc3[2] = {T(0), T(0)};
 #pragma unroll
@@ -261,18 +288,16 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
     grid_barrier(a.bar, a.err);
     grid_totals<2>(partB, tot);
     ++it;
-    rr = tot[0];
-    const double beta = tot[1] / rz;
-    rz = tot[1];
-    if (*(volatile int*)a.err != 0 || !isfinite(rr)) {
-      flag = 2;
-      break;
+    if (threadIdx.x == 0) {
+      rr = tot[0];
+      s_scal = (T)(tot[1] / rz);
+      rz = tot[1];
+      s_flag = (*(volatile int*)a.err != 0 || !isfinite(rr)) ? 2 : (rr <= tol2 ? 1 : 0);
     }
-    if (rr <= tol2) {
-      flag = 1;
-      break;
-    }
-    const T bt = (T)beta;
+    __syncthreads();
+    flag = s_flag;
+    if (flag != 0) break;
+    const T bt = s_scal;
 #pragma unroll
     for (int c = 0; c < PPT; ++c) {
       if (!((live >> c) & 1u)) continue;
@@ -291,22 +316,29 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
     a.sc[S_BREAK] = flag == 2 ? 1 : 0;
     a.sc[S_DONE] = 1;
   }
-  (void)s_flag;
 }
 
 struct GridPlan {
-  int grid = 0, epb = 0;
+  int grid = 0, epb = 0, spb = 0;
   size_t smem = 0;
   const void* f = nullptr;
 };
 
 // A plan for PPT points per thread: the grid it needs must be co-resident and at
 // most two blocks per SM (fewer arrivals per barrier).
+// shared memory of a block: factors (when staged) and the segment staging room
+template <typename GT, bool SMEM_G>
+size_t grid_smem(int epb, int spb) {
+  const size_t g = SMEM_G ? ((size_t)epb * 7 * NPC3 * sizeof(GT) + 15) / 16 * 16 : 0;
+  return g + (size_t)(spb + 1) * 4 + (size_t)8 * spb * 4 + (size_t)spb;
+}
+
 template <typename T, typename GT, int PPT, bool SMEM_G>
-bool plan_for(int E, int nsm, GridPlan* out) {
+bool plan_for(int E, int64_t nseg, int nsm, GridPlan* out) {
   const int epb = (PPT * GT_THREADS) / NPC3;                 // elements one block can hold
   const int grid = (E + epb - 1) / epb;
-  const size_t smem = SMEM_G ? (size_t)epb * 7 * NPC3 * sizeof(GT) : 0;
+  const int spb = (int)((nseg + grid - 1) / grid) + 1;
+  const size_t smem = grid_smem<GT, SMEM_G>(epb, spb);
   if (smem > 200 * 1024) return false;
   const void* f = (const void*)k_coarse_grid<T, GT, PPT, SMEM_G>;
   if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -321,19 +353,20 @@ bool plan_for(int E, int nsm, GridPlan* out) {
   if (per_sm < 1 || grid > std::min(per_sm, 2) * nsm) return false;
   out->grid = grid;
   out->epb = (E + grid - 1) / grid;                          // spread the elements evenly
-  out->smem = SMEM_G ? (size_t)out->epb * 7 * NPC3 * sizeof(GT) : 0;
+  out->spb = spb;
+  out->smem = grid_smem<GT, SMEM_G>(out->epb, spb);
   out->f = f;
   return true;
 }
 
 template <typename T, typename GT>
-bool make_plan(int E, int nsm, GridPlan* pl) {
-  if (plan_for<T, GT, 1, true>(E, nsm, pl) || plan_for<T, GT, 2, true>(E, nsm, pl) ||
-      plan_for<T, GT, 4, true>(E, nsm, pl) || plan_for<T, GT, 8, true>(E, nsm, pl) ||
-      plan_for<T, GT, 16, true>(E, nsm, pl) || plan_for<T, GT, 8, false>(E, nsm, pl) ||
-      plan_for<T, GT, 16, false>(E, nsm, pl))
+bool make_plan(int E, int64_t nseg, int nsm, GridPlan* pl) {
+  if (plan_for<T, GT, 1, true>(E, nseg, nsm, pl) || plan_for<T, GT, 2, true>(E, nseg, nsm, pl) ||
+      plan_for<T, GT, 4, true>(E, nseg, nsm, pl) || plan_for<T, GT, 8, true>(E, nseg, nsm, pl) ||
+      plan_for<T, GT, 16, true>(E, nseg, nsm, pl) || plan_for<T, GT, 8, false>(E, nseg, nsm, pl) ||
+      plan_for<T, GT, 16, false>(E, nseg, nsm, pl))
     return true;
-  if constexpr (sizeof(T) == 4) return plan_for<T, GT, 32, false>(E, nsm, pl);   // FP64 would spill
+  if constexpr (sizeof(T) == 4) return plan_for<T, GT, 32, false>(E, nseg, nsm, pl);   // FP64 would spill
   return false;
 }
 
@@ -346,7 +379,7 @@ int launch_grid(const Level& L, const GT* G, const void* b, void* x, void* pglob
   SEM_CUDA_TRY(cudaGetDevice(&dev));
   SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   GridPlan pl;
-  if (!make_plan<T, GT>(L.E, nsm, &pl)) return SEM_OK;   // does not fit: the caller falls back
+  if (!make_plan<T, GT>(L.E, L.n_seg, nsm, &pl)) return SEM_OK;   // does not fit: the caller falls back
   if (pl.grid > COARSE_GRID_MAX) return SEM_OK;
   GridArgs a{};
   a.E = L.E;
@@ -367,6 +400,7 @@ int launch_grid(const Level& L, const GT* G, const void* b, void* x, void* pglob
   a.tol = tol;
   a.maxit = maxit;
   a.epb = pl.epb;
+  a.spb = pl.spb;
   a.part = part;
   a.bar = bar;
   a.err = err;

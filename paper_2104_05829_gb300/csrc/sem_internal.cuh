@@ -112,6 +112,9 @@ struct Level {
   int32_t* sch_poff = nullptr;    // CSR offsets into sch_psrc
   int32_t* sch_psrc = nullptr;    // staged slots per point, in slot order
   int64_t sch_npts = 0;
+  // on-chip cluster coarse solve: (CTA rank << 24 | offset) of every gather-scatter copy
+  int32_t* cl_loc = nullptr;      // [n_seg_idx]
+  int cl_loc_epc = 0;             // elements per CTA the locations were computed for
 };
 
 // Device scalar slots (double) used by the Krylov kernels.

@@ -223,7 +223,7 @@ void free_level(Level& L) {
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
-                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc};
+                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.cl_loc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -345,7 +345,7 @@ void sem_default_opts(sem_opts* o) {
   o->cheb_lmax_factor = 1.1;
   o->lanczos_steps = 10;
   o->lanczos_seed = 1;
-  o->coarse_tol = 1e-2;
+  o->coarse_tol = 1e-1;
   o->coarse_maxit = 100;
   o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
   o->smoother = SEM_SMOOTH_JACOBI;
@@ -411,7 +411,7 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   else sem_default_opts(&o);
   if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
       (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM) || o.coarse_mode < SEM_COARSE_AUTO ||
-      o.coarse_mode > SEM_COARSE_KERNELS) {
+      o.coarse_mode > SEM_COARSE_GRID) {
     set_detail("invalid smoother / Lanczos / coarse-solve options");
     return SEM_EINVAL;
   }

@@ -235,14 +235,16 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   Level& L = C.lev[l];
   VecSet v = vecs(L, prec);
   double* sc = C.scal + 1 * S_NSLOTS;
-  // order 1: the whole solve in one cooperative launch over the GPU, or (FP32 /
-  // BF16-factor V-cycles) in one launch on one thread-block cluster
+  // order 1: the whole solve in one cooperative launch over the whole GPU, or in
+  // one launch on one thread-block cluster with the problem on chip (FP32 /
+  // BF16-factor V-cycles)
   bool used = false;
-  if (C.opts.coarse_mode == SEM_COARSE_AUTO)
+  const int mode = C.opts.coarse_mode;
+  if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_GRID)
     SEM_TRY(coarse_grid_solve(L, prec, b, x, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
                               C.opts.coarse_maxit, sc, C.cg_part, C.cg_bar, C.cg_err, s, &used));
   if (used) return SEM_OK;
-  if (C.opts.coarse_mode != SEM_COARSE_KERNELS)
+  if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_CLUSTER)
     SEM_TRY(coarse_cluster_solve(L, prec, b, x, v.r, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
                                  C.opts.coarse_maxit, sc, s, &used));
   if (used) return SEM_OK;

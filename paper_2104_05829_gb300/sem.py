@@ -52,7 +52,7 @@ def default_opts(**kw) -> L.SemOpts:
             o.smoother = {"jacobi": L.SEM_SMOOTH_JACOBI, "asm": L.SEM_SMOOTH_ASM}.get(v, v)
         elif k == "coarse_mode":
             o.coarse_mode = {"auto": L.SEM_COARSE_AUTO, "cluster": L.SEM_COARSE_CLUSTER,
-                             "kernels": L.SEM_COARSE_KERNELS}.get(v, v)
+                             "kernels": L.SEM_COARSE_KERNELS, "grid": L.SEM_COARSE_GRID}.get(v, v)
         elif not hasattr(o, k):
             raise KeyError(k)
         else:
