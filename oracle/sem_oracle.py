@@ -20,6 +20,7 @@ solver"), Section 2.3 ("Spectral Element Discretization"), Section 3.2
 * Jacobi-PCG, flexible PCG, Chebyshev-Jacobi smoothing and the p-multigrid
   V-cycle with orders N, N/2 .. 1 (Section 3.4),
 * projection of successive right-hand sides onto earlier solutions (Section 3.4),
+* the dealiased advection operator on Gauss points (Sections 2.1 and 3.3),
 * the adjoint gradient of a mass-weighted loss with respect to nodal h1.
 
 Global (unique-node) vectors are used for every solver here; the library works
@@ -1077,6 +1078,77 @@ def solve_projected(level: Level, proj: Projection, b, h1=1.0, h2=0.0, tol=1e-8,
     res.xbar = xbar
     res.x = x
     return res
+
+
+# ----------------------------------------------------------------------------
+# Dealiased advection operator (Section 2.1, eq. stdadv and eq. hyp, whose
+# nonlinear term is evaluated on N_q^3 quadrature points; Section 3.3 "High-Order
+# Kernels" on its N_q^3 dealiased evaluation)
+# ----------------------------------------------------------------------------
+
+
+def cubature_points(N: int, nq: int | None = None):
+    """Gauss-Legendre rule of the dealiased evaluation: nq = ceil(3 (N+1) / 2) points
+    by default (N=7 -> 12), exact for polynomials of degree <= 2 nq - 1
+    (numpy.polynomial.legendre.leggauss)."""
+    if nq is None:
+        nq = (3 * (N + 1) + 1) // 2
+    z, w = np.polynomial.legendre.leggauss(nq)
+    return z, w
+
+
+@dataclass
+class Cubature:
+    """Per-level data of the dealiased evaluation: the interpolation Im from the
+    GLL nodes to the Gauss points, the derivative matrix Dq on the Gauss points,
+    and at every Gauss point of every element the nine factors
+    Gq[e, d, m] = w_q J_q dr_d/dx_m (quadrature weight, Jacobian, inverse metric)."""
+    nq: int
+    z: np.ndarray
+    w: np.ndarray
+    Im: np.ndarray
+    Dq: np.ndarray
+    Gq: np.ndarray
+
+
+def cubature_setup(level: "Level", nq: int | None = None) -> Cubature:
+    """The isoparametric map (eq. xijk) interpolated to the Gauss points and
+    differentiated there (the map is a degree-N polynomial, so both steps are
+    exact); the 3x3 metric is inverted pointwise (numpy.linalg.inv)."""
+    z, w = cubature_points(level.N, nq)
+    Im = interp_matrix(level.xi, z)
+    Dq = lagrange_deriv_matrix(z)
+    X = [interp_local(c - c[:, :1, :1, :1], Im) for c in (level.x, level.y, level.z)]
+    d = [grad_ref(c, Dq) for c in X]                        # d[m][q] = dx_m / dr_q
+    Jm = np.stack([np.stack(d[m], -1) for m in range(3)], -2)   # (..., m, q)
+    det = np.linalg.det(Jm)
+    inv = np.linalg.inv(Jm)                                  # (..., q, m) = dr_q / dx_m
+    w3 = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    Gq = np.moveaxis(inv, (-2, -1), (1, 2)) * (w3 * det)[:, None, None]
+    return Cubature(len(z), z, w, Im, Dq, Gq)
+
+
+def advect_local(level: "Level", cub: Cubature, cL, uL):
+    """w_L = the dealiased weak advection term of u with advecting field c, element
+    by element: (C u)_i = sum_q w_q J_q phi_i(x_q) (c . grad u)(x_q).
+
+    c at the Gauss points is interpolated from its nodal values, the
+    contravariant field chat_d = w_q J_q sum_m (dr_d/dx_m) c_m is formed, u is
+    interpolated and differentiated on the Gauss points, and the pointwise
+    product sum_d chat_d du/dr_d is projected back with the transposed
+    interpolation. cL: (3, E, NP, NP, NP); uL: (E, NP, NP, NP)."""
+    cq = [interp_local(cL[m], cub.Im) for m in range(3)]
+    chat = [sum(cub.Gq[:, dd, m] * cq[m] for m in range(3)) for dd in range(3)]
+    uq = interp_local(uL, cub.Im)
+    ur, us, ut = grad_ref(uq, cub.Dq)
+    conv = chat[0] * ur + chat[1] * us + chat[2] * ut
+    return interp_local_T(conv, cub.Im)
+
+
+def advect_assembled(level: "Level", cub: Cubature, cL, ug):
+    """Q^T C_L Q u on a global vector (no Dirichlet mask: the advection term is explicit)."""
+    uL = q_gather(ug, level.node).reshape(level.x.shape)
+    return q_scatter(advect_local(level, cub, cL, uL), level.node, level.n_G)
 
 
 # ----------------------------------------------------------------------------
