@@ -31,6 +31,7 @@ METRIC = "GDOF/s of Ax+gather-scatter and PCG time-to-1e-8 at N=7, vs HBM roofli
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4          # GB300 nominal 1.25 TFLOP/s FP64 at 2.07 GHz over 152 SMs
 SM_MAX_MHZ = 2070.0
+FP32_TFLOPS = 72.0                # FFMA microbenchmark on this machine's GB300 (2 flops per FMA)
 
 
 def ax_flops_per_element(N: int, helmholtz: bool = True) -> int:
@@ -339,6 +340,43 @@ def proj_bench(ctx_cls, args, dev):
     return out
 
 
+def advect_work_per_element(N: int, ncomp: int = 3):
+    """Multiply-adds of the dealiased advection kernel per element (sum-factorised, as
+    executed): wind interpolation and contravariant combination once, then per
+    component interpolation, three Gauss-point derivatives, the product and the
+    transposed interpolation; and the bytes it must move (factors, c, u, w)."""
+    NP, NQ = N + 1, (3 * (N + 1) + 1) // 2
+    interp = NQ * NP ** 3 + NQ ** 2 * NP ** 2 + NQ ** 3 * NP
+    mac = 3 * interp + 9 * NQ ** 3 + ncomp * (2 * interp + 3 * NQ ** 4 + 3 * NQ ** 3)
+    words = 9 * NQ ** 3 + (3 + 2 * ncomp) * NP ** 3
+    return 2 * mac, words
+
+
+def advect_bench(ctx, u, nG, E, N, stream, pk, steps=(5, 50)):
+    """Dealiased u . grad u (three components) on the Ax box, FP64 and FP32."""
+    import torch
+
+    flops_e, words_e = advect_work_per_element(N)
+    out = {"workload": f"dealiased advection u . grad u, 3 components, {E} elements N={N}, "
+                       f"nq={(3 * (N + 1) + 1) // 2} Gauss points per direction",
+           "flops_per_element": flops_e, "words_per_element": words_e}
+    for prec, dt, nstep in (("fp64", torch.float64, steps[0]), ("fp32", torch.float32, steps[1])):
+        c = torch.stack([u, 0.5 * u, -u]).to(dt).contiguous()
+        uu = c.clone()
+        w = torch.empty_like(c)
+        fn = lambda: ctx.advect(c, uu, w, prec=prec)
+        fn()   # builds the cubature factors on the first call
+        fn()
+        t = time_events(fn, nstep, stream) / nstep
+        fl = flops_e * E / t / 1e12
+        byt = words_e * E * (8 if prec == "fp64" else 4) / t / 1e9
+        peak = pk["fp64_tflops"] if prec == "fp64" else FP32_TFLOPS
+        out[prec] = {"ms": 1e3 * t, "GDOF_per_s": 3 * nG / t / 1e9, "tflops": fl, "alu_peak_tflops": peak,
+                     "alu_frac": fl / peak, "achieved_gbs": byt, "hbm_frac": byt / pk["hbm_gbs"]}
+        del c, uu, w
+    return out
+
+
 def sweep_orders(ctx_cls, dev, stream, steps=100):
     """Ax+gs throughput across orders at about 16.8M local points (nearest cube of elements)."""
     import torch
@@ -383,6 +421,7 @@ def main():
     ap.add_argument("--solve-48", action="store_true", help="also time the 48^3-element (56.6M-point) solve")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-proj", action="store_true", help="skip the successive-RHS projection sequence")
+    ap.add_argument("--no-advect", action="store_true", help="skip the dealiased advection timing")
     ap.add_argument("--coarse-tol", type=float, default=None, help="coarse Jacobi-PCG tolerance (default 1e-2)")
     ap.add_argument("--coarse-mode", default="auto", choices=["auto", "cluster", "grid", "kernels"],
                     help="execution of the coarse Jacobi-PCG (same algorithm)")
@@ -496,6 +535,8 @@ def main():
             "value": world * nG * args.steps / tv / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * tv / args.steps,
             "ax_kernel_ms": 1e3 * tva / args.steps, "dtype": "f32x2" if other else "f64",
             "ax_kernel_tflops_paper_count": flops / (tva / args.steps) / 1e12}}
+    if not args.no_advect:
+        line["advection"] = advect_bench(ctx, u, nG, E, 7, stream, pk)
     ctx.close()
     if args.sweep:
         line["sweep"] = sweep_orders(SemContext, dev, stream)

@@ -278,6 +278,23 @@ int sem_proj_update(sem_proj* pj, const sem_coef* coef, int flags, const double*
 int sem_solve_proj(sem_ctx* ctx, sem_proj* pj, const double* f_L, const sem_coef* coef, double tol, int maxit,
                    int precond, int prec, int rhs_flags, double* u_L, sem_info* info, void* stream);
 
+/* Dealiased advection operator (Section 2.1: the nonlinear term of eq. stdadv and the
+ * hyperbolic substeps of eq. hyp; Section 3.3: evaluated on N_q^3 quadrature points):
+ * for each of ncomp fields u, w = C(c) u with
+ *   (C u)_i = sum_q w_q J_q phi_i(x_q) (c . grad u)(x_q),
+ * q over nq^3 Gauss-Legendre points per element, nq = ceil(3 (N+1) / 2) (N = 7: 12),
+ * on the fine level; element-local (SEM_ADV_LOCAL) or summed over the copies of each
+ * node, Q Q^T C_L u (SEM_ADV_ASSEMBLE; no Dirichlet mask: the term is explicit).
+ * c_L: 3 DEVICE L-vectors back to back ([3][nL], components x, y, z); u_L and w_L:
+ * ncomp L-vectors back to back ([ncomp][nL]); w_L must not alias c_L or u_L.
+ * prec SEM_FP64 (double vectors) or SEM_FP32 (float vectors, FP32 arithmetic).
+ * The cubature factors w J dr/dx at the Gauss points are built on the first call
+ * (synchronous; 9 nq^3 values per element in FP64 and FP32). Compiled for 2 <= N <= 8. */
+#define SEM_ADV_LOCAL 0
+#define SEM_ADV_ASSEMBLE 1
+int sem_advect(sem_ctx* ctx, int prec, const void* c_L, const void* u_L, void* w_L, int ncomp, int flags,
+               void* stream);
+
 /* Adjoint gradient with respect to nodal h1 (no counterpart in the paper's
  * solver; built on eq. Ae): g_L = -sum_{m,m'} (D_m lam)(G_mm')(D_m' u) at every
  * local point, with G excluding h1. For L = loss(u(h1)), A lam = dL/du gives

@@ -26,6 +26,7 @@ SEM_RHS_NODAL, SEM_RHS_ASSEMBLED, SEM_X0_GIVEN, SEM_OUTER_PAIRS = 0, 1, 2, 4
 SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
+SEM_ADV_LOCAL, SEM_ADV_ASSEMBLE = 0, 1
 SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS, SEM_COARSE_GRID = 0, 1, 2, 3
 
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "sem_cheb_smooth": (_I, [_P, _I, _P, _P, _I, _P]),
     "sem_vcycle": (_I, [_P, _P, _P, _P]),
     "sem_asm_apply": (_I, [_P, _I, _I, _P, _P, _D, _D, _P]),
+    "sem_advect": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
     "sem_get_lmax": (_I, [_P, _P, _I]),
     "sem_solve": (_I, [_P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),
     "sem_solve_proj": (_I, [_P, _P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),

@@ -1,0 +1,428 @@
+// Dealiased advection operator (Section 2.1, the nonlinear term of eq. stdadv
+// and the hyperbolic substeps of eq. hyp; Section 3.3 "High-Order Kernels":
+// the term is evaluated on N_q^3 quadrature points with a 2-D thread plane and
+// one register line per thread).
+//
+// For an advecting field c (three components) and ncomp advected fields u:
+//   (C u)_i = sum_q w_q J_q phi_i(x_q) (c . grad u)(x_q),
+// q over nq^3 Gauss-Legendre points, nq = ceil(3 (N+1) / 2). Per element:
+//   1. each c_m is interpolated to the Gauss points (three sum-factorised
+//      passes, the last one into the thread's register line along t);
+//   2. the contravariant wind chat_d = sum_m Gq[d][m] c_m with the cubature
+//      factors Gq = w J dr_d/dx_m (stored per point, set up once) -- kept in
+//      registers and reused for every advected component (Section 3.3);
+//   3. for each u: interpolation as in 1, derivatives on the Gauss points
+//      (t along the register line, r and s through shared memory), the
+//      pointwise product sum_d chat_d du/dr_d, and the transposed interpolation
+//      back to the GLL points (three passes).
+// Thread (a, b) of the nq x nq plane owns the Gauss points (a, b, *).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sem_internal.cuh"
+
+namespace sem {
+
+namespace {
+
+// Gauss-Legendre nodes (ascending) and weights: roots of P_n by Newton's method
+// from x = cos(pi (4i - 1) / (4n + 2)), weights 2 / ((1 - x^2) P_n'(x)^2).
+void host_gauss(int n, double* z, double* w) {
+  for (int i = 1; i <= n; ++i) {
+    double x = std::cos(M_PI * (4.0 * i - 1.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 1; k < n; ++k) {
+        const double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = n == 0 ? 1.0 : p1, pm1 = n == 0 ? 0.0 : p0;
+      dp = n * (x * pn - pm1) / (x * x - 1.0);
+      const double step = pn / dp;
+      x -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    z[n - i] = x;
+    w[n - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  for (int i = 0; i < n / 2; ++i) {   // exact symmetry
+    const double a = 0.5 * (z[n - 1 - i] - z[i]), b = 0.5 * (w[i] + w[n - 1 - i]);
+    z[n - 1 - i] = a;
+    z[i] = -a;
+    w[i] = w[n - 1 - i] = b;
+  }
+  if (n % 2 == 1) z[n / 2] = 0.0;
+}
+
+// Dq[a][b] = h_b'(z_a) for the cardinal polynomials on the nodes z (barycentric form).
+void host_deriv(int n, const double* z, double* D) {
+  std::vector<double> lam(n, 1.0);
+  for (int b = 0; b < n; ++b)
+    for (int c = 0; c < n; ++c)
+      if (c != b) lam[b] /= (z[b] - z[c]);
+  for (int a = 0; a < n; ++a) {
+    double diag = 0.0;
+    for (int b = 0; b < n; ++b) {
+      if (a == b) continue;
+      D[a * n + b] = lam[b] / lam[a] / (z[a] - z[b]);
+      diag -= D[a * n + b];
+    }
+    D[a * n + a] = diag;
+  }
+}
+
+constexpr int nq_of(int NP) { return (3 * NP + 1) / 2; }
+
+template <int NP>
+struct AdvShape {
+  static constexpr int NQ = nq_of(NP);
+  static constexpr int T = NQ * NQ;   // threads per element
+};
+
+// 1-D operators in shared memory: Im [NQ][NP] (GLL -> Gauss), Dq [NQ][NQ]
+template <typename T, int NP, int NQ>
+__device__ __forceinline__ void load_ops(const T* __restrict__ Im, const T* __restrict__ Dq, T* sI, T* sD) {
+  for (int q = threadIdx.x; q < NQ * NP; q += blockDim.x) sI[q] = Im[q];
+  for (int q = threadIdx.x; q < NQ * NQ; q += blockDim.x) sD[q] = Dq[q];
+}
+
+// Interpolate the element's nodal field src (in shared memory, [k][j][i]) to the
+// Gauss points; thread (a, b) receives its t-line out[c] = f(z_a, z_b, z_c).
+// Uses t1 [NP][NP][NQ] in shared memory.
+template <typename T, int NP, int NQ>
+__device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, int a, int b, T (&out)[NQ]) {
+  // r-pass: t1[k][j][a] for j < NP (threads with b < NP)
+  if (b < NP) {
+#pragma unroll 2
+    for (int k = 0; k < NP; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) acc = fma(sI[a * NP + i], src[(k * NP + b) * NP + i], acc);
+      t1[(k * NP + b) * NQ + a] = acc;
+    }
+  }
+  __syncthreads();
+  // s-pass into registers: t2[k] = sum_j I[b][j] t1[k][j][a]
+  T t2[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc = fma(sI[b * NP + j], t1[(k * NP + j) * NQ + a], acc);
+    t2[k] = acc;
+  }
+  // t-pass in registers
+#pragma unroll
+  for (int c = 0; c < NQ; ++c) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc = fma(sI[c * NP + k], t2[k], acc);
+    out[c] = acc;
+  }
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(AdvShape<NP>::T)
+    k_advect(int E, int ncomp, int64_t nL, const T* __restrict__ cv, const T* __restrict__ uv,
+             const T* __restrict__ Gq, const T* __restrict__ Im, const T* __restrict__ Dq, T* __restrict__ wv) {
+  constexpr int NQ = AdvShape<NP>::NQ, NP3 = NP * NP * NP, NQ2 = NQ * NQ, NQ3 = NQ2 * NQ;
+  __shared__ T sI[NQ * NP];
+  __shared__ T sD[NQ * NQ];
+  __shared__ T s_src[NP3];              // nodal field; later the result planes
+  __shared__ T s_t1[NP * NP * NQ];      // first interpolation pass; later the last projection pass
+  __shared__ T s_U[NQ3];                // u on the Gauss points; later the t-projected planes
+  const int e = blockIdx.x;
+  const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
+  load_ops<T, NP, NQ>(Im, Dq, sI, sD);
+  const size_t eb = (size_t)e * NP3;
+  const T* G = Gq + (size_t)e * 9 * NQ3 + b * NQ + a;
+  // 1-2. contravariant wind on this thread's line
+  T ch0[NQ], ch1[NQ], ch2[NQ];
+#pragma unroll
+  for (int c = 0; c < NQ; ++c) ch0[c] = ch1[c] = ch2[c] = T(0);
+  for (int m = 0; m < 3; ++m) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = cv[(size_t)m * nL + eb + q];
+    __syncthreads();
+    T cf[NQ];
+    to_gauss<T, NP, NQ>(s_src, s_t1, sI, a, b, cf);
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+      ch0[c] = fma(G[(0 * 3 + m) * NQ3 + c * NQ2], cf[c], ch0[c]);
+      ch1[c] = fma(G[(1 * 3 + m) * NQ3 + c * NQ2], cf[c], ch1[c]);
+      ch2[c] = fma(G[(2 * 3 + m) * NQ3 + c * NQ2], cf[c], ch2[c]);
+    }
+  }
+  // 3. every advected component
+  for (int comp = 0; comp < ncomp; ++comp) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = uv[(size_t)comp * nL + eb + q];
+    __syncthreads();
+    T uf[NQ];
+    to_gauss<T, NP, NQ>(s_src, s_t1, sI, a, b, uf);
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) s_U[(c * NQ + b) * NQ + a] = uf[c];
+    __syncthreads();
+    T conv[NQ];
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+      T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) {
+        ur = fma(sD[a * NQ + m], s_U[(c * NQ + b) * NQ + m], ur);
+        us = fma(sD[b * NQ + m], s_U[(c * NQ + m) * NQ + a], us);
+        ut = fma(sD[c * NQ + m], uf[m], ut);
+      }
+      conv[c] = ch0[c] * ur + ch1[c] * us + ch2[c] * ut;
+    }
+    // back to the GLL points: t-pass from registers into v2[k][b][a] (s_U reused)
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) acc = fma(sI[c * NP + k], conv[c], acc);
+      s_U[(k * NQ + b) * NQ + a] = acc;
+    }
+    __syncthreads();
+    // s-pass: v1[k][j][a] = sum_b I[b][j] v2[k][b][a] (threads with b < NP own j = b)
+    if (b < NP) {
+#pragma unroll 2
+      for (int k = 0; k < NP; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc = fma(sI[q * NP + b], s_U[(k * NQ + q) * NQ + a], acc);
+        s_t1[(k * NP + b) * NQ + a] = acc;
+      }
+    }
+    __syncthreads();
+    // r-pass: w[k][j][i] = sum_a I[a][i] v1[k][j][a] (threads (i, j) = (a, b) with a, b < NP)
+    if (a < NP && b < NP) {
+      T* out = wv + (size_t)comp * nL + eb;
+#pragma unroll 2
+      for (int k = 0; k < NP; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc = fma(sI[q * NP + a], s_t1[(k * NP + b) * NQ + q], acc);
+        out[(k * NP + b) * NP + a] = acc;
+      }
+    }
+  }
+}
+
+// Cubature factors Gq[e][d][m][point] = w_q J_q dr_d/dx_m at the Gauss points:
+// the coordinates (relative to the element's first node) interpolated and
+// differentiated on the Gauss points, the 3x3 metric inverted by cofactors.
+template <int NP>
+__global__ void __launch_bounds__(AdvShape<NP>::T)
+    k_cub_geom(int E, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+               const double* __restrict__ Im, const double* __restrict__ Dq, const double* __restrict__ wq,
+               double* __restrict__ Gq, float* __restrict__ Gq32, int* bad) {
+  constexpr int NQ = AdvShape<NP>::NQ, NP3 = NP * NP * NP, NQ2 = NQ * NQ, NQ3 = NQ2 * NQ;
+  __shared__ double sI[NQ * NP];
+  __shared__ double sD[NQ * NQ];
+  __shared__ double s_src[NP3];
+  __shared__ double s_t1[NP * NP * NQ];
+  __shared__ double s_X[NQ3];
+  const int e = blockIdx.x;
+  const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
+  load_ops<double, NP, NQ>(Im, Dq, sI, sD);
+  const size_t eb = (size_t)e * NP3;
+  double Jl[3][3][NQ];   // Jl[m][d][c] = dx_m / dr_d at Gauss point (a, b, c)
+  const double* X[3] = {x, y, z};
+  for (int m = 0; m < 3; ++m) {
+    __syncthreads();
+    const double x0 = X[m][eb];
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = X[m][eb + q] - x0;
+    __syncthreads();
+    double line[NQ];
+    to_gauss<double, NP, NQ>(s_src, s_t1, sI, a, b, line);
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) s_X[(c * NQ + b) * NQ + a] = line[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+      double dr = 0, ds = 0, dt = 0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        dr = fma(sD[a * NQ + q], s_X[(c * NQ + b) * NQ + q], dr);
+        ds = fma(sD[b * NQ + q], s_X[(c * NQ + q) * NQ + a], ds);
+        dt = fma(sD[c * NQ + q], line[q], dt);
+      }
+      Jl[m][0][c] = dr;
+      Jl[m][1][c] = ds;
+      Jl[m][2][c] = dt;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NQ; ++c) {
+    double J[3][3];   // J[m][d] = dx_m / dr_d
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) J[m][d] = Jl[m][d][c];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(det > 0.0)) atomicExch(bad, 1);
+    // R[d][m] = det * dr_d/dx_m (the adjugate); w J dr_d/dx_m = w R[d][m]
+    double R[3][3];
+    R[0][0] = c00;
+    R[1][0] = c01;
+    R[2][0] = c02;
+    R[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    R[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    R[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    R[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    R[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    R[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double wgt = wq[a] * wq[b] * wq[c];
+    const size_t pt = (size_t)e * 9 * NQ3 + (c * NQ + b) * NQ + a;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double v = wgt * R[d][m];
+        Gq[pt + (d * 3 + m) * NQ3] = v;
+        if (Gq32) Gq32[pt + (d * 3 + m) * NQ3] = (float)v;
+      }
+  }
+}
+
+template <int NP>
+int cub_geom_launch(const Level& L, const double* Im, const double* Dq, const double* wq, double* Gq, float* Gq32,
+                    int* bad, cudaStream_t s) {
+  k_cub_geom<NP><<<L.E, AdvShape<NP>::T, 0, s>>>(L.E, L.x, L.y, L.z, Im, Dq, wq, Gq, Gq32, bad);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+template <typename T, int NP>
+int advect_launch(const Level& L, const T* c, const T* u, T* w, int ncomp, const T* Gq, const T* Im,
+                  const T* Dq, cudaStream_t s) {
+  k_advect<T, NP><<<L.E, AdvShape<NP>::T, 0, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
+
+#define ADV_DISPATCH(NPV, CALL) \
+  case NPV: return CALL;
+
+}  // namespace
+
+// Build the cubature data of level 0 (Gauss rule, interpolation and derivative
+// matrices, Gq in FP64 and FP32). Synchronous.
+int advect_build(Ctx& C, cudaStream_t s) {
+  Level& L = C.lev[0];
+  if (C.adv.ready) return SEM_OK;
+  if (L.N < 2 || L.N > 8) {
+    set_detail("the dealiased advection operator is compiled for 2 <= N <= 8 (order %d)", L.N);
+    return SEM_EINVAL;
+  }
+  const int NP = L.NP, NQ = nq_of(NP);
+  std::vector<double> z(NQ), w(NQ), Im(NQ * NP), Dq(NQ * NQ);
+  host_gauss(NQ, z.data(), w.data());
+  host_interp(NP, L.xi, NQ, z.data(), Im.data());
+  host_deriv(NQ, z.data(), Dq.data());
+  std::vector<float> Im32(Im.begin(), Im.end()), Dq32(Dq.begin(), Dq.end());
+  AdvData& A = C.adv;
+  A.nq = NQ;
+  const size_t ng = (size_t)L.E * 9 * NQ * NQ * NQ;
+  auto dm = [&](void** p, size_t bytes) -> int {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      cudaGetLastError();
+      set_detail("cudaMalloc of %zu bytes failed (advection cubature data)", bytes);
+      return SEM_ENOMEM;
+    }
+    return SEM_OK;
+  };
+  SEM_TRY(dm((void**)&A.Gq, ng * 8));
+  SEM_TRY(dm((void**)&A.Gq32, ng * 4));
+  SEM_TRY(dm((void**)&A.Im, Im.size() * 8));
+  SEM_TRY(dm((void**)&A.Dq, Dq.size() * 8));
+  SEM_TRY(dm((void**)&A.wq, NQ * 8));
+  SEM_TRY(dm((void**)&A.Im32, Im.size() * 4));
+  SEM_TRY(dm((void**)&A.Dq32, Dq.size() * 4));
+  SEM_CUDA_TRY(cudaMemcpyAsync(A.Im, Im.data(), Im.size() * 8, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(A.Dq, Dq.data(), Dq.size() * 8, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(A.wq, w.data(), NQ * 8, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(A.Im32, Im32.data(), Im32.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(A.Dq32, Dq32.data(), Dq32.size() * 4, cudaMemcpyHostToDevice, s));
+  int* bad = nullptr;
+  SEM_TRY(dm((void**)&bad, sizeof(int)));
+  SEM_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  int rc = SEM_OK;
+  switch (NP) {
+    case 3: rc = cub_geom_launch<3>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    case 4: rc = cub_geom_launch<4>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    case 5: rc = cub_geom_launch<5>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    case 6: rc = cub_geom_launch<6>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    case 7: rc = cub_geom_launch<7>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    case 8: rc = cub_geom_launch<8>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+    default: rc = cub_geom_launch<9>(L, A.Im, A.Dq, A.wq, A.Gq, A.Gq32, bad, s); break;
+  }
+  int h_bad = 0;
+  if (rc == SEM_OK) {
+    if (cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_detail("advection cubature setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = SEM_ECUDA;
+    }
+  }
+  cudaFree(bad);
+  if (rc != SEM_OK) return rc;
+  if (h_bad) {
+    set_detail("non-positive Jacobian at a Gauss point");
+    return SEM_EMESH;
+  }
+  A.ready = true;
+  return SEM_OK;
+}
+
+void advect_free(AdvData& A) {
+  void* ptrs[] = {A.Gq, A.Gq32, A.Im, A.Dq, A.wq, A.Im32, A.Dq32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  A = AdvData();
+}
+
+int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s) {
+  const Level& L = C.lev[0];
+  const AdvData& A = C.adv;
+  if (prec == SEM_FP64) {
+    const double *cc = (const double*)c, *uu = (const double*)u;
+    double* ww = (double*)w;
+    switch (L.NP) {
+      ADV_DISPATCH(3, (advect_launch<double, 3>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(4, (advect_launch<double, 4>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(5, (advect_launch<double, 5>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(6, (advect_launch<double, 6>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(7, (advect_launch<double, 7>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(8, (advect_launch<double, 8>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(9, (advect_launch<double, 9>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      default: break;
+    }
+  } else {
+    const float *cc = (const float*)c, *uu = (const float*)u;
+    float* ww = (float*)w;
+    switch (L.NP) {
+      ADV_DISPATCH(3, (advect_launch<float, 3>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(4, (advect_launch<float, 4>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(5, (advect_launch<float, 5>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(6, (advect_launch<float, 6>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(7, (advect_launch<float, 7>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(8, (advect_launch<float, 8>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(9, (advect_launch<float, 9>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      default: break;
+    }
+  }
+  set_detail("the dealiased advection operator is compiled for 2 <= N <= 8");
+  return SEM_EINVAL;
+}
+
+}  // namespace sem

@@ -14,9 +14,11 @@
 // Sums: per-thread partials (FP32 in the FP32 solve), block sums in FP64
 // written to a partial array; after the barrier every block adds all block
 // partials in the same fixed order, so all blocks hold the same bits and take
-// the same branches. The barrier is a generation counter with bounded waiting:
-// a block that waits longer than about a second sets an error flag, after
-// which every barrier returns at once and the solve reports a breakdown.
+// the same branches. The grid barrier has no contended counter: each block
+// publishes an epoch in its own flag, block 0 waits for all flags in parallel
+// and releases the epoch. Waits are bounded: a block that waits longer than
+// about a second sets an error flag, after which every barrier returns at once
+// and the solve reports a breakdown.
 // The algorithm is the multi-kernel one: x0 = 0, r = b, z = D^-1 r, stop when
 // (r, r) <= tol^2 (b, b) or after maxit iterations.
 #include <algorithm>
@@ -51,7 +53,7 @@ struct GridArgs {
   int epb;                          // elements per block
   int spb;                          // gather-scatter segments per block (upper bound, staged in shared memory)
   double* part;                     // [3][gridDim.x] block partials
-  unsigned* bar;                    // [0] arrival count, [1] generation
+  unsigned* bar;                    // [gridDim.x] arrival epochs, then [1] the released epoch
   int* err;                         // barrier timeout flag
   double* sc;                       // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
 };
@@ -61,32 +63,44 @@ __device__ __forceinline__ double fval(double v) { return v; }
 __device__ __forceinline__ float fval(float v) { return v; }
 __device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Grid barrier with bounded waiting (generation counter).
-__device__ void grid_barrier(unsigned* bar, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    if (*(volatile int*)err == 0) {
-      const unsigned g = *gen;
-      __threadfence();
-      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicExch(bar + 1, g + 1);
-      } else {
-        unsigned spins = 0;
-        while (*gen == g) {
-          if (*(volatile int*)err != 0) break;   // another block gave up: stop waiting
-          __nanosleep(64);
-          if (++spins > (1u << 24)) {   // about a second
-            atomicExch(err, 1);
-            break;
-          }
-        }
-      }
-      __threadfence();
+// Wait until *v >= target, at most about a second; then raise the error flag.
+__device__ __forceinline__ void wait_at_least(const unsigned* v, unsigned target, int* err) {
+  unsigned spins = 0;
+  while (*(const volatile unsigned*)v < target) {
+    if (*(volatile int*)err != 0) return;   // another block gave up: stop waiting
+    __nanosleep(32);
+    if (++spins > (1u << 25)) {
+      atomicExch(err, 1);
+      return;
     }
   }
+}
+
+// Grid barrier without a contended counter: every block publishes the barrier's
+// epoch in its own flag; block 0's threads wait for all flags in parallel and
+// then publish the epoch in `gen`, which the other blocks wait for. Epochs grow
+// by one per barrier from 0 (flags and gen are zeroed before the launch).
+// Waits are bounded (wait_at_least); after a timeout every barrier returns at once.
+__device__ void grid_barrier(unsigned* flags, unsigned* gen, int* err, unsigned& epoch) {
+  ++epoch;
+  __syncthreads();
+  const bool live = *(volatile int*)err == 0;
+  if (threadIdx.x == 0 && live) {
+    __threadfence();
+    atomicExch(flags + blockIdx.x, epoch);
+  }
+  if (blockIdx.x == 0) {
+    if (live)
+      for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) wait_at_least(flags + q, epoch, err);
+    __syncthreads();
+    if (threadIdx.x == 0 && live) {
+      __threadfence();
+      atomicExch(gen, epoch);
+    }
+  } else if (threadIdx.x == 0 && live) {
+    wait_at_least(gen, epoch, err);
+  }
+  if (threadIdx.x == 0) __threadfence();
   __syncthreads();
 }
 
@@ -186,10 +200,11 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
       }
     }
   }
+  unsigned epoch = 0;                            // barriers passed
   double* partA = a.part;                        // (p, w)
   double* partB = a.part + gridDim.x;            // (r, r), (r, z): 2 * gridDim.x
   block_partial<2>(acc2, partB);
-  grid_barrier(a.bar, a.err);
+  grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
   grid_totals<2>(partB, tot);
   // scalars (identical in every block)
   double bb = tot[0], rz = tot[1], rr = bb;
@@ -241,7 +256,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
         if ((solo >> c) & 1u) acc1[0] = fma(u, wv, acc1[0]);
       }
     }
-    grid_barrier(a.bar, a.err);
+    grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
     // 2. gather-scatter of shared / Dirichlet nodes, with (p, w) at their owner copies
     for (int sg = threadIdx.x; sg < ns; sg += GT_THREADS) {
       const int bgn = g_off[sg], end = g_off[sg + 1];
@@ -256,7 +271,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
       }
     }
     block_partial<1>(acc1, partA);
-    grid_barrier(a.bar, a.err);
+    grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
     grid_totals<1>(partA, tot);
     // the FP64 scalar recurrences run in thread 0 only (FP64 division is slow on this part)
     if (threadIdx.x == 0) {
@@ -285,7 +300,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
       }
     }
     block_partial<2>(acc3, partB);
-    grid_barrier(a.bar, a.err);
+    grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
     grid_totals<2>(partB, tot);
     ++it;
     if (threadIdx.x == 0) {
@@ -407,7 +422,7 @@ int launch_grid(const Level& L, const GT* G, const void* b, void* x, void* pglob
   a.sc = sc;
   Mat64 D = L.D;
   void* args[] = {&a, &D};
-  SEM_CUDA_TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(bar, 0, (pl.grid + 1) * sizeof(unsigned), s));
   SEM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
   SEM_CUDA_TRY(cudaLaunchCooperativeKernel(pl.f, dim3(pl.grid), dim3(GT_THREADS), args, pl.smem, s));
   *used = true;

@@ -135,6 +135,16 @@ enum Scal {
   S_NSLOTS
 };
 
+// Dealiased advection data of level 0 (advect.cu; built on first use)
+struct AdvData {
+  bool ready = false;
+  int nq = 0;
+  double* Gq = nullptr;      // [E][9][nq^3] w J dr_d/dx_m at the Gauss points
+  float* Gq32 = nullptr;
+  double *Im = nullptr, *Dq = nullptr, *wq = nullptr;   // GLL -> Gauss interpolation, Gauss derivative, weights
+  float *Im32 = nullptr, *Dq32 = nullptr;
+};
+
 struct Ctx {
   int device = 0;
   int nlevels = 0;
@@ -154,9 +164,10 @@ struct Ctx {
   cudaEvent_t ev = nullptr;
   cudaEvent_t cev[2] = {nullptr, nullptr};   // coarse-solve batch markers
   double* h_done = nullptr;                  // pinned, 2 slots
+  AdvData adv;
   // scratch of the whole-GPU coarse solve
   double* cg_part = nullptr;                 // [3 * COARSE_GRID_MAX]
-  unsigned* cg_bar = nullptr;                // [2]
+  unsigned* cg_bar = nullptr;                // [COARSE_GRID_MAX + 1]
   int* cg_err = nullptr;                     // [1]
 };
 
@@ -184,7 +195,7 @@ int coarse_cluster_solve(const Level& L, int prec, const void* b, void* x, void*
                          cudaStream_t s, bool* used);
 
 // ---- coarse_grid.cu: one-launch coarse Jacobi-PCG over the whole GPU (cooperative launch)
-constexpr int COARSE_GRID_MAX = 2048;   // largest grid; scratch: part[3 * COARSE_GRID_MAX], bar[2], err[1]
+constexpr int COARSE_GRID_MAX = 2048;   // largest grid; scratch: part[3 * COARSE_GRID_MAX], bar[COARSE_GRID_MAX + 1], err[1]
 int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p, void* w, const void* dinv,
                       double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
                       cudaStream_t s, bool* used);
@@ -233,6 +244,11 @@ int cheb_w_update(const Level& L, int prec, const void* z, void* x, void* d, dou
                   bool x_zero, cudaStream_t s);
 int arnoldi_lmax_asm(Ctx& C, int l, double h1, double h2, const double* v0, int steps, cudaStream_t s,
                      double* lam);
+
+// ---- advect.cu: dealiased advection operator
+int advect_build(Ctx& C, cudaStream_t s);
+void advect_free(AdvData& A);
+int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s);
 
 // ---- proj.cu: projection of successive right-hand sides
 struct Proj;

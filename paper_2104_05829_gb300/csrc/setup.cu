@@ -371,6 +371,7 @@ void sem_free(sem_ctx* h) {
   Ctx* C = reinterpret_cast<Ctx*>(h);
   if (!C) return;
   for (int l = 0; l < SEM_MAX_LEVELS; ++l) free_level(C->lev[l]);
+  advect_free(C->adv);
   void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->dr, C->t,
                   C->cg_part, C->cg_bar, C->cg_err};
   for (void* p : ptrs)
@@ -487,7 +488,7 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   STEP(dmalloc(&C->red_part, RED_BLOCKS * 4));
   STEP(dmalloc(&C->red_ticket, 1));
   STEP(dmalloc(&C->cg_part, 3 * COARSE_GRID_MAX));
-  STEP(dmalloc(&C->cg_bar, 2));
+  STEP(dmalloc(&C->cg_bar, COARSE_GRID_MAX + 1));
   STEP(dmalloc(&C->cg_err, 1));
   CUSTEP(cudaMemsetAsync(C->red_ticket, 0, sizeof(unsigned), s));
   STEP(dmalloc(&C->scal, 4 * S_NSLOTS));

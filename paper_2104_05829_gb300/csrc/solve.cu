@@ -491,6 +491,26 @@ int sem_asm_apply(sem_ctx* h, int level, int prec, const void* r, void* z, doubl
   return asm_weight(L, prec, z, s);
 }
 
+int sem_advect(sem_ctx* h, int prec, const void* c, const void* u, void* w, int ncomp, int flags, void* stream) {
+  Ctx* C = ctx_of(h);
+  SEM_TRY(check_level(C, 0));
+  if (!c || !u || !w || w == u || w == c || ncomp < 1 || (prec != SEM_FP64 && prec != SEM_FP32) ||
+      (flags & ~SEM_ADV_ASSEMBLE)) {
+    set_detail("sem_advect: NULL or aliased vector, ncomp < 1, precision other than FP64/FP32, or unknown flag");
+    return SEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SEM_TRY(advect_build(*C, s));
+  SEM_TRY(advect_apply(*C, prec, c, u, w, ncomp, s));
+  if (flags & SEM_ADV_ASSEMBLE) {
+    const Level& L = C->lev[0];
+    const size_t esz = prec == SEM_FP64 ? 8 : 4;
+    for (int q = 0; q < ncomp; ++q)
+      SEM_TRY(gs_apply(L, prec, static_cast<char*>(w) + (size_t)q * L.nL * esz, false, s));
+  }
+  return SEM_OK;
+}
+
 int sem_vcycle(sem_ctx* h, const double* r, double* z, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));

@@ -218,6 +218,19 @@ class SemContext:
                 "sem_asm_apply")
         return z
 
+    def advect(self, c, u, w=None, assemble=False, prec="fp64", stream=None):
+        """Dealiased advection w = C(c) u (sem_advect). c: (3, nL) tensor; u: (ncomp, nL) or (nL,)."""
+        dt = torch.float64 if _PREC[prec] in _F64 else torch.float32
+        squeeze = u.dim() == 1
+        u2 = u.reshape(-1, self.nL)
+        w = torch.empty_like(u2) if w is None else w.reshape(-1, self.nL)
+        ncomp = u2.shape[0]
+        L.check(self._lib.sem_advect(self._h, _PREC[prec], _dev(c, dt, 3 * self.nL, "c"),
+                                     _dev(u2, dt, ncomp * self.nL, "u"), _dev(w, dt, ncomp * self.nL, "w"), ncomp,
+                                     L.SEM_ADV_ASSEMBLE if assemble else L.SEM_ADV_LOCAL, _stream(stream)),
+                "sem_advect")
+        return w.reshape(-1) if squeeze else w
+
     def vcycle(self, r, z=None, stream=None):
         z = torch.empty_like(r) if z is None else z
         L.check(self._lib.sem_vcycle(self._h, _dev(r, torch.float64, self.nL, "r"),
