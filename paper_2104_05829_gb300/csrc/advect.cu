@@ -94,25 +94,33 @@ __device__ __forceinline__ void load_ops(const T* __restrict__ Im, const T* __re
 // Uses t1 [NP][NP][NQ] in shared memory.
 template <typename T, int NP, int NQ>
 __device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, int a, int b, T (&out)[NQ]) {
-  // r-pass: t1[k][j][a] for j < NP (threads with b < NP)
+  // r-pass: t1[k][j][a] for j < NP (threads with b < NP); row a of I held in registers
   if (b < NP) {
+    T ia[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ia[i] = sI[a * NP + i];
 #pragma unroll 2
     for (int k = 0; k < NP; ++k) {
       T acc = T(0);
 #pragma unroll
-      for (int i = 0; i < NP; ++i) acc = fma(sI[a * NP + i], src[(k * NP + b) * NP + i], acc);
+      for (int i = 0; i < NP; ++i) acc = fma(ia[i], src[(k * NP + b) * NP + i], acc);
       t1[(k * NP + b) * NQ + a] = acc;
     }
   }
   __syncthreads();
-  // s-pass into registers: t2[k] = sum_j I[b][j] t1[k][j][a]
+  // s-pass into registers: t2[k] = sum_j I[b][j] t1[k][j][a]; row b of I in registers
   T t2[NP];
+  {
+    T ib[NP];
 #pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    T acc = T(0);
+    for (int j = 0; j < NP; ++j) ib[j] = sI[b * NP + j];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fma(sI[b * NP + j], t1[(k * NP + j) * NQ + a], acc);
-    t2[k] = acc;
+    for (int k = 0; k < NP; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc = fma(ib[j], t1[(k * NP + j) * NQ + a], acc);
+      t2[k] = acc;
+    }
   }
   // t-pass in registers
 #pragma unroll
@@ -134,6 +142,10 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
   __shared__ T s_src[NP3];              // nodal field; later the result planes
   __shared__ T s_t1[NP * NP * NQ];      // first interpolation pass; later the last projection pass
   __shared__ T s_U[NQ3];                // u on the Gauss points; later the t-projected planes
+  // FP32: the wind lives in shared memory during the component loop (fewer registers, more
+  // resident blocks); FP64 keeps it in registers (its shared memory would not fit)
+  constexpr bool WIND_SMEM = sizeof(T) == 4 && NP <= 8;
+  __shared__ T s_ch[WIND_SMEM ? 3 * NQ3 : 1];
   const int e = blockIdx.x;
   const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
   load_ops<T, NP, NQ>(Im, Dq, sI, sD);
@@ -156,6 +168,15 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
       ch2[c] = fma(G[(2 * 3 + m) * NQ3 + c * NQ2], cf[c], ch2[c]);
     }
   }
+  if (WIND_SMEM) {
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) {
+      const int pt = (c * NQ + b) * NQ + a;
+      s_ch[pt] = ch0[c];
+      s_ch[NQ3 + pt] = ch1[c];
+      s_ch[2 * NQ3 + pt] = ch2[c];
+    }
+  }
   // 3. every advected component
   for (int comp = 0; comp < ncomp; ++comp) {
     __syncthreads();
@@ -167,16 +188,29 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     for (int c = 0; c < NQ; ++c) s_U[(c * NQ + b) * NQ + a] = uf[c];
     __syncthreads();
     T conv[NQ];
-#pragma unroll
-    for (int c = 0; c < NQ; ++c) {
-      T ur = T(0), us = T(0), ut = T(0);
+    {
+      T da[NQ], db[NQ];   // rows a and b of the Gauss derivative matrix
 #pragma unroll
       for (int m = 0; m < NQ; ++m) {
-        ur = fma(sD[a * NQ + m], s_U[(c * NQ + b) * NQ + m], ur);
-        us = fma(sD[b * NQ + m], s_U[(c * NQ + m) * NQ + a], us);
-        ut = fma(sD[c * NQ + m], uf[m], ut);
+        da[m] = sD[a * NQ + m];
+        db[m] = sD[b * NQ + m];
       }
-      conv[c] = ch0[c] * ur + ch1[c] * us + ch2[c] * ut;
+#pragma unroll
+      for (int c = 0; c < NQ; ++c) {
+        T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          ur = fma(da[m], s_U[(c * NQ + b) * NQ + m], ur);
+          us = fma(db[m], s_U[(c * NQ + m) * NQ + a], us);
+          ut = fma(sD[c * NQ + m], uf[m], ut);
+        }
+        if (WIND_SMEM) {
+          const int pt = (c * NQ + b) * NQ + a;
+          conv[c] = s_ch[pt] * ur + s_ch[NQ3 + pt] * us + s_ch[2 * NQ3 + pt] * ut;
+        } else {
+          conv[c] = ch0[c] * ur + ch1[c] * us + ch2[c] * ut;
+        }
+      }
     }
     // back to the GLL points: t-pass from registers into v2[k][b][a] (s_U reused)
     __syncthreads();
@@ -190,11 +224,14 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     __syncthreads();
     // s-pass: v1[k][j][a] = sum_b I[b][j] v2[k][b][a] (threads with b < NP own j = b)
     if (b < NP) {
+      T cb[NQ];   // column b of I
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) cb[q] = sI[q * NP + b];
 #pragma unroll 2
       for (int k = 0; k < NP; ++k) {
         T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc = fma(sI[q * NP + b], s_U[(k * NQ + q) * NQ + a], acc);
+        for (int q = 0; q < NQ; ++q) acc = fma(cb[q], s_U[(k * NQ + q) * NQ + a], acc);
         s_t1[(k * NP + b) * NQ + a] = acc;
       }
     }
@@ -202,11 +239,14 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     // r-pass: w[k][j][i] = sum_a I[a][i] v1[k][j][a] (threads (i, j) = (a, b) with a, b < NP)
     if (a < NP && b < NP) {
       T* out = wv + (size_t)comp * nL + eb;
+      T ca[NQ];   // column a of I
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) ca[q] = sI[q * NP + a];
 #pragma unroll 2
       for (int k = 0; k < NP; ++k) {
         T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc = fma(sI[q * NP + a], s_t1[(k * NP + b) * NQ + q], acc);
+        for (int q = 0; q < NQ; ++q) acc = fma(ca[q], s_t1[(k * NP + b) * NQ + q], acc);
         out[(k * NP + b) * NP + a] = acc;
       }
     }
