@@ -5,12 +5,16 @@
 // SMs. Here every SM takes a slice of whole elements; per-point Krylov vectors
 // (x, r, p, the Jacobi weights and flags) live in registers for the whole
 // solve, each block's geometric factors are staged once in shared memory, and
-// phases are separated by a grid barrier. An iteration has three barriers:
-//   1. element operator w_L = A_L p (registers + shared memory, warp shuffles), then barrier;
+// phases are separated by a grid barrier. The iteration is the Chronopoulos-Gear
+// form of Jacobi-PCG (the same iterates in exact arithmetic, one reduction per
+// iteration), which needs two barriers:
+//   1. x, r, p and s = A p updated with the previous scalars; u = D^-1 r;
+//      (r, u) and (r, r); element operator w_L = A_L u (registers + shared
+//      memory, warp shuffles); barrier;
 //   2. gather-scatter of the shared nodes (segments split across blocks) with
-//      the (p, w) products of their owner copies, then barrier;
-//   3. alpha from the reduced (p, w); x += alpha p, r -= alpha w; (r, r) and
-//      (r, D^-1 r), then barrier; beta, convergence; p = D^-1 r + beta p.
+//      the (w, u) products of their owner copies; barrier; the three sums give
+//      the convergence test, beta = (r, u)_new / (r, u) and
+//      alpha = (r, u)_new / ((w, u) - beta (r, u)_new / alpha_old).
 // Sums: per-thread partials (FP32 in the FP32 solve), block sums in FP64
 // written to a partial array; after the barrier every block adds all block
 // partials in the same fixed order, so all blocks hold the same bits and take
@@ -19,8 +23,8 @@
 // and releases the epoch. Waits are bounded: a block that waits longer than
 // about a second sets an error flag, after which every barrier returns at once
 // and the solve reports a breakdown.
-// The algorithm is the multi-kernel one: x0 = 0, r = b, z = D^-1 r, stop when
-// (r, r) <= tol^2 (b, b) or after maxit iterations.
+// As in the multi-kernel solve: x0 = 0, r = b, stop when (r, r) <= tol^2 (b, b)
+// or after maxit iterations.
 #include <algorithm>
 
 #include "sem_internal.cuh"
@@ -63,15 +67,18 @@ __device__ __forceinline__ double fval(double v) { return v; }
 __device__ __forceinline__ float fval(float v) { return v; }
 __device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Wait until *v >= target, at most about a second; then raise the error flag.
+// Wait until *v >= target, at most about a second of SM clock (2^31 cycles); then
+// raise the error flag. The flag is re-read every 64 polls.
 __device__ __forceinline__ void wait_at_least(const unsigned* v, unsigned target, int* err) {
-  unsigned spins = 0;
+  const long long t0 = clock64();
+  unsigned polls = 0;
   while (*(const volatile unsigned*)v < target) {
-    if (*(volatile int*)err != 0) return;   // another block gave up: stop waiting
-    __nanosleep(32);
-    if (++spins > (1u << 25)) {
-      atomicExch(err, 1);
-      return;
+    if ((++polls & 63u) == 0) {
+      if (*(volatile int*)err != 0) return;   // another block gave up: stop waiting
+      if (clock64() - t0 > (1ll << 31)) {
+        atomicExch(err, 1);
+        return;
+      }
     }
   }
 }
@@ -152,9 +159,9 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
   int32_t* s_off = reinterpret_cast<int32_t*>(s_raw + g_bytes);    // [spb + 1]
   int32_t* s_idx = s_off + a.spb + 1;                               // [8 * spb]
   uint8_t* s_dir = reinterpret_cast<uint8_t*>(s_idx + 8 * a.spb);  // [spb]
-  __shared__ double tot[2];
-  __shared__ int s_flag;     // 0 go on, 1 converged, 2 breakdown
-  __shared__ T s_scal;       // alpha or beta, computed once per block by thread 0
+  __shared__ double tot[3];
+  __shared__ int s_flag;     // 0 go on, 1 converged, 2 breakdown, 3 iteration cap
+  __shared__ T s_al, s_be;   // alpha and beta, computed once per block by thread 0
   const T* b = static_cast<const T*>(a.b);
   T* xg = static_cast<T*>(a.x);
   T* pg = static_cast<T*>(a.p_glob);
@@ -177,40 +184,27 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
   const T dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
   const T ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;
   const T h1 = (T)a.h1, h2 = (T)a.h2;
-  T x[PPT], r[PPT], p[PPT], dinv[PPT];
+  // Chronopoulos-Gear form of Jacobi-PCG (one reduction per iteration): with
+  // u = D^-1 r and w = A u, gamma = (r, u), delta = (w, u);
+  //   p = u + beta p, s = w + beta s (= A p), x += alpha p, r -= alpha s,
+  //   beta = gamma_new / gamma, alpha = gamma_new / (delta - beta gamma_new / alpha_old).
+  T x[PPT], r[PPT], p[PPT], sv[PPT], dinv[PPT];
   unsigned solo = 0, own = 0, live = 0;   // bit c: point c is an owner / an owner of a one-copy node / exists
-  T acc2[2] = {T(0), T(0)};
 #pragma unroll
   for (int c = 0; c < PPT; ++c) {
     const int lp = threadIdx.x + c * GT_THREADS;
-    x[c] = r[c] = p[c] = dinv[c] = T(0);
+    x[c] = r[c] = p[c] = sv[c] = dinv[c] = T(0);
     if (lp < npts) {
       const int64_t l = p0 + lp;
       live |= 1u << c;
-      const T bl = b[l];
       dinv[c] = dv[l];
-      r[c] = bl;
-      p[c] = dinv[c] * bl;
-      __stcg(pg + l, p[c]);
+      r[c] = b[l];
       if (a.own[l]) {
         own |= 1u << c;
         if (a.mult[l] == 1) solo |= 1u << c;
-        acc2[0] = fma(bl, bl, acc2[0]);
-        acc2[1] = fma(bl, p[c], acc2[1]);
       }
     }
   }
-  unsigned epoch = 0;                            // barriers passed
-  double* partA = a.part;                        // (p, w)
-  double* partB = a.part + gridDim.x;            // (r, r), (r, z): 2 * gridDim.x
-  block_partial<2>(acc2, partB);
-  grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
-  grid_totals<2>(partB, tot);
-  // scalars (identical in every block)
-  double bb = tot[0], rz = tot[1], rr = bb;
-  const double tol2 = a.tol * a.tol * bb;
-  int flag = rr <= tol2 ? 1 : 0;   // 0 go on, 1 converged, 2 breakdown
-  int it = 0;
   const int64_t s0 = a.nseg * blockIdx.x / gridDim.x, s1 = a.nseg * (blockIdx.x + 1) / gridDim.x;
   // stage the block's gather-scatter segments once (they never change); a block whose
   // segments hold more copies than the staging room reads them from global memory
@@ -226,14 +220,39 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
   const int32_t* g_off = staged ? s_off : a.seg_off + s0;    // offsets relative to g_idx
   const int32_t* g_idx = staged ? s_idx : a.seg_idx;
   const uint8_t* g_dir = staged ? s_dir : a.seg_dir + s0;
-  while (flag == 0 && it < a.maxit) {
-    // 1. element operator w = A_L p on this block's elements
-    T acc1[1] = {T(0)};
+  unsigned epoch = 0;                 // barriers passed
+  // scalar state, held by thread 0 only (FP64 division is slow on this part)
+  double bb = 0, rr = 0, gam = 0, alpha_old = 0, tol2 = 0;
+  int flag = 0, it = 0;               // flag: 0 go on, 1 converged, 2 breakdown, 3 iteration cap
+  T al = T(0), be = T(0);
+  bool first = true;
+  while (true) {
+    // update with the scalars of the previous pass (none in the first pass)
+    if (!first) {
+#pragma unroll
+      for (int c = 0; c < PPT; ++c) {
+        if (!((live >> c) & 1u)) continue;
+        const int64_t l = p0 + threadIdx.x + c * GT_THREADS;
+        p[c] = fma(be, p[c], dinv[c] * r[c]);
+        sv[c] = fma(be, sv[c], __ldcg(w + l));
+        x[c] = fma(al, p[c], x[c]);
+        r[c] = fma(-al, sv[c], r[c]);
+      }
+    }
+    // u = D^-1 r; (r, u), (r, r); w = A_L u; (w, u) on one-copy owners
+    T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int c = 0; c < PPT; ++c) {
       const int lp = threadIdx.x + c * GT_THREADS;
       const bool lv = (live >> c) & 1u;
-      const T u = p[c];
+      const T u = dinv[c] * r[c];
+      if (lv) {
+        __stcg(pg + p0 + lp, u);
+        if ((own >> c) & 1u) {
+          acc[0] = fma(r[c], u, acc[0]);
+          acc[1] = fma(r[c], r[c], acc[1]);
+        }
+      }
       const T ur = di_s * u + di_o * __shfl_xor_sync(0xffffffffu, u, 1);
       const T us = dj_s * u + dj_o * __shfl_xor_sync(0xffffffffu, u, 2);
       const T ut = dk_s * u + dk_o * __shfl_xor_sync(0xffffffffu, u, 4);
@@ -253,11 +272,11 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
       wv += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
       if (lv) {
         __stcg(w + p0 + lp, wv);
-        if ((solo >> c) & 1u) acc1[0] = fma(u, wv, acc1[0]);
+        if ((solo >> c) & 1u) acc[2] = fma(u, wv, acc[2]);
       }
     }
     grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
-    // 2. gather-scatter of shared / Dirichlet nodes, with (p, w) at their owner copies
+    // gather-scatter of shared / Dirichlet nodes, with (w, u) at their owner copies
     for (int sg = threadIdx.x; sg < ns; sg += GT_THREADS) {
       const int bgn = g_off[sg], end = g_off[sg + 1];
       if (g_dir[sg]) {
@@ -267,58 +286,44 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
         for (int q = bgn + 1; q < end; ++q) sum += __ldcg(w + g_idx[q]);
         if (end - bgn > 1)
           for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], sum);
-        acc1[0] = fma(__ldcg(pg + g_idx[bgn]), sum, acc1[0]);
+        acc[2] = fma(__ldcg(pg + g_idx[bgn]), sum, acc[2]);
       }
     }
-    block_partial<1>(acc1, partA);
+    block_partial<3>(acc, a.part);
     grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
-    grid_totals<1>(partA, tot);
-    // the FP64 scalar recurrences run in thread 0 only (FP64 division is slow on this part)
+    grid_totals<3>(a.part, tot);
     if (threadIdx.x == 0) {
-      const double pw = tot[0];
-      const bool bad = *(volatile int*)a.err != 0 || !(pw > 0.0) || !isfinite(pw);
-      s_flag = bad ? 2 : 0;
-      s_scal = bad ? T(0) : (T)(rz / pw);
-    }
-    __syncthreads();
-    if (s_flag != 0) {
-      flag = 2;
-      break;
-    }
-    const T alpha = s_scal;
-    // 3. x += alpha p, r -= alpha w; (r, r), (r, D^-1 r)
-    T acc3[2] = {T(0), T(0)};
-#pragma unroll
-    for (int c = 0; c < PPT; ++c) {
-      if (!((live >> c) & 1u)) continue;
-      const int64_t l = p0 + threadIdx.x + c * GT_THREADS;
-      x[c] = fma(alpha, p[c], x[c]);
-      r[c] = fma(-alpha, __ldcg(w + l), r[c]);
-      if ((own >> c) & 1u) {
-        acc3[0] = fma(r[c], r[c], acc3[0]);
-        acc3[1] = fma(r[c], dinv[c] * r[c], acc3[1]);
+      const double gnew = tot[0], del = tot[2];
+      rr = tot[1];
+      if (first) {
+        bb = rr;
+        tol2 = a.tol * a.tol * bb;
+      } else {
+        ++it;
       }
-    }
-    block_partial<2>(acc3, partB);
-    grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
-    grid_totals<2>(partB, tot);
-    ++it;
-    if (threadIdx.x == 0) {
-      rr = tot[0];
-      s_scal = (T)(tot[1] / rz);
-      rz = tot[1];
-      s_flag = (*(volatile int*)a.err != 0 || !isfinite(rr)) ? 2 : (rr <= tol2 ? 1 : 0);
+      int f = 0;
+      double alpha = 0, beta = 0;
+      if (*(volatile int*)a.err != 0 || !isfinite(rr)) f = 2;
+      else if (rr <= tol2) f = 1;
+      else if (it >= a.maxit) f = 3;
+      else {
+        beta = first ? 0.0 : gnew / gam;
+        const double den = first ? del : del - beta * gnew / alpha_old;
+        alpha = gnew / den;
+        if (!(den > 0.0) || !(gnew > 0.0) || !isfinite(alpha)) f = 2;
+      }
+      gam = gnew;
+      alpha_old = alpha;
+      s_flag = f;
+      s_al = (T)alpha;
+      s_be = (T)beta;
     }
     __syncthreads();
     flag = s_flag;
+    al = s_al;
+    be = s_be;
+    first = false;
     if (flag != 0) break;
-    const T bt = s_scal;
-#pragma unroll
-    for (int c = 0; c < PPT; ++c) {
-      if (!((live >> c) & 1u)) continue;
-      p[c] = fma(bt, p[c], dinv[c] * r[c]);
-      __stcg(pg + p0 + threadIdx.x + c * GT_THREADS, p[c]);
-    }
   }
 #pragma unroll
   for (int c = 0; c < PPT; ++c)
