@@ -12,7 +12,9 @@
 //      factors Gq = w J dr_d/dx_m (stored per point, set up once) -- kept in
 //      registers and reused for every advected component (Section 3.3);
 //   3. for each u: interpolation as in 1, derivatives on the Gauss points
-//      (t along the register line, r and s through shared memory), the
+//      (t along the thread's register line; r and s on lines of the Gauss-point
+//      array in shared memory, each thread differentiating one whole line; all
+//      three in even-odd form with the coefficients as kernel parameters), the
 //      pointwise product sum_d chat_d du/dr_d, and the transposed interpolation
 //      back to the GLL points (three passes).
 // Thread (a, b) of the nq x nq plane owns the Gauss points (a, b, *).
@@ -74,13 +76,22 @@ void host_deriv(int n, const double* z, double* D) {
   }
 }
 
-constexpr int nq_of(int NP) { return (3 * NP + 1) / 2; }
+__host__ __device__ constexpr int nq_of(int NP) { return (3 * NP + 1) / 2; }
 
 template <int NP>
 struct AdvShape {
   static constexpr int NQ = nq_of(NP);
-  static constexpr int T = NQ * NQ;   // threads per element
+  static constexpr int T = NQ * NQ;                      // threads per element
+  static constexpr int RS = NQ % 2 == 0 ? NQ + 1 : NQ;   // padded row stride of the Gauss-point arrays
+  static constexpr int PS = NQ * RS;                     // plane stride
 };
+
+// dynamic shared memory of k_advect<T, NP>
+template <typename T, int NP>
+constexpr size_t advect_smem() {
+  constexpr int NQ = AdvShape<NP>::NQ, PS = AdvShape<NP>::PS;
+  return sizeof(T) * ((size_t)NQ * NP + NQ * NQ + NP * NP * NP + NP * NP * NQ + 2 * NQ * PS + 3 * NQ * NQ * NQ);
+}
 
 // 1-D operators in shared memory: Im [NQ][NP] (GLL -> Gauss), Dq [NQ][NQ]
 template <typename T, int NP, int NQ>
@@ -93,7 +104,8 @@ __device__ __forceinline__ void load_ops(const T* __restrict__ Im, const T* __re
 // Gauss points; thread (a, b) receives its t-line out[c] = f(z_a, z_b, z_c).
 // Uses t1 [NP][NP][NQ] in shared memory.
 template <typename T, int NP, int NQ>
-__device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, int a, int b, T (&out)[NQ]) {
+__device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, const T* cI, int a, int b,
+                                         T (&out)[NQ]) {
   // r-pass: t1[k][j][a] for j < NP (threads with b < NP); row a of I held in registers
   if (b < NP) {
     T ia[NP];
@@ -122,59 +134,104 @@ __device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, int a
       t2[k] = acc;
     }
   }
-  // t-pass in registers
+  // t-pass in registers (cI: the interpolation matrix at compile-time indices)
 #pragma unroll
   for (int c = 0; c < NQ; ++c) {
     T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) acc = fma(sI[c * NP + k], t2[k], acc);
+    for (int k = 0; k < NP; ++k) acc = fma(cI[c * NP + k], t2[k], acc);
     out[c] = acc;
   }
 }
 
+// 1-D operators passed by value (kernel parameters: with fully unrolled loops the
+// coefficients become constant-bank operands, no shared-memory loads): the
+// interpolation Im [NQ][NP] and the even-odd pieces of the Gauss derivative Dq,
+// which is centro-antisymmetric (Dq[NQ-1-a][NQ-1-b] = -Dq[a][b]): with
+// H = NQ / 2, s_b = v_b + v_{NQ-1-b} and d_b = v_b - v_{NQ-1-b},
+//   ev_a = sum_b ep[a][b] s_b (+ mc[a] v_H if NQ is odd), od_a = sum_b op[a][b] d_b,
+//   (Dq v)_a = ev_a + od_a, (Dq v)_{NQ-1-a} = od_a - ev_a, (Dq v)_H = sum_b mr[b] d_b (NQ odd),
+// ep = (Dq[a][b] + Dq[a][NQ-1-b]) / 2, op = (Dq[a][b] - Dq[a][NQ-1-b]) / 2.
 template <typename T, int NP>
-__global__ void __launch_bounds__(AdvShape<NP>::T)
+struct AdvOps {
+  static constexpr int NQ = nq_of(NP), H = NQ / 2;
+  T Im[NQ * NP];
+  T ep[H * H], op[H * H], mc[H > 0 ? H : 1], mr[H > 0 ? H : 1];
+};
+
+template <typename T, int NP>
+__device__ __forceinline__ void eo_deriv(const AdvOps<T, NP>& P, const T (&v)[nq_of(NP)], T (&o)[nq_of(NP)]) {
+  constexpr int NQ = nq_of(NP), H = NQ / 2, N = NQ - 1;
+  T sm[H], df[H];
+#pragma unroll
+  for (int b = 0; b < H; ++b) {
+    sm[b] = v[b] + v[N - b];
+    df[b] = v[b] - v[N - b];
+  }
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    T ev = T(0), od = T(0);
+#pragma unroll
+    for (int b = 0; b < H; ++b) {
+      ev = fma(P.ep[a * H + b], sm[b], ev);
+      od = fma(P.op[a * H + b], df[b], od);
+    }
+    if (NQ % 2 == 1) ev = fma(P.mc[a], v[H], ev);
+    o[a] = ev + od;
+    o[N - a] = od - ev;
+  }
+  if (NQ % 2 == 1) {
+    T m = T(0);
+#pragma unroll
+    for (int b = 0; b < H; ++b) m = fma(P.mr[b], df[b], m);
+    o[H] = m;
+  }
+}
+
+// resident blocks requested from the register allocator: three in FP32 (13.5 warps per
+// SM; two at N = 8, where three spill), two in FP64 (a few hundred bytes of spills,
+// measured 1.26x faster at N = 7 than one block with no spills)
+template <typename T, int NP>
+__host__ __device__ constexpr int adv_min_blocks() {
+  return sizeof(T) == 4 ? (NP <= 8 ? 3 : 2) : 2;
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
     k_advect(int E, int ncomp, int64_t nL, const T* __restrict__ cv, const T* __restrict__ uv,
-             const T* __restrict__ Gq, const T* __restrict__ Im, const T* __restrict__ Dq, T* __restrict__ wv) {
+             const T* __restrict__ Gq, const T* __restrict__ Im, const T* __restrict__ Dq, T* __restrict__ wv,
+             AdvOps<T, NP> P) {
   constexpr int NQ = AdvShape<NP>::NQ, NP3 = NP * NP * NP, NQ2 = NQ * NQ, NQ3 = NQ2 * NQ;
-  __shared__ T sI[NQ * NP];
-  __shared__ T sD[NQ * NQ];
-  __shared__ T s_src[NP3];              // nodal field; later the result planes
-  __shared__ T s_t1[NP * NP * NQ];      // first interpolation pass; later the last projection pass
-  __shared__ T s_U[NQ3];                // u on the Gauss points; later the t-projected planes
-  // FP32: the wind lives in shared memory during the component loop (fewer registers, more
-  // resident blocks); FP64 keeps it in registers (its shared memory would not fit)
-  constexpr bool WIND_SMEM = sizeof(T) == 4 && NP <= 8;
-  __shared__ T s_ch[WIND_SMEM ? 3 * NQ3 : 1];
+  constexpr int RS = AdvShape<NP>::RS, PS = AdvShape<NP>::PS;
+  // dynamic shared memory (advect_smem<T, NP>() bytes):
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  T* sI = reinterpret_cast<T*>(s_raw);   // [NQ * NP] interpolation, runtime-indexed rows and columns
+  T* sD = sI + NQ * NP;                  // [NQ * NQ]
+  T* s_src = sD + NQ * NQ;               // [NP3] nodal field
+  T* s_t1 = s_src + NP3;                 // [NP * NP * NQ] first interpolation pass; last projection pass
+  T* s_U = s_t1 + NP * NP * NQ;          // [NQ * PS] u on the Gauss points; later the t-projected planes
+  T* s_R = s_U + NQ * PS;                // [NQ * PS] a derivative, one direction at a time
+  T* s_ch = s_R + NQ * PS;               // [3 * NQ3] the contravariant wind
   const int e = blockIdx.x;
   const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
   load_ops<T, NP, NQ>(Im, Dq, sI, sD);
   const size_t eb = (size_t)e * NP3;
   const T* G = Gq + (size_t)e * 9 * NQ3 + b * NQ + a;
-  // 1-2. contravariant wind on this thread's line
-  T ch0[NQ], ch1[NQ], ch2[NQ];
+  // 1-2. contravariant wind at this thread's points, kept in shared memory
+  const int pt0 = b * NQ + a;   // point (a, b, c) at pt0 + c * NQ2
 #pragma unroll
-  for (int c = 0; c < NQ; ++c) ch0[c] = ch1[c] = ch2[c] = T(0);
+  for (int c = 0; c < NQ; ++c) s_ch[pt0 + c * NQ2] = s_ch[NQ3 + pt0 + c * NQ2] = s_ch[2 * NQ3 + pt0 + c * NQ2] = T(0);
   for (int m = 0; m < 3; ++m) {
     __syncthreads();
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = cv[(size_t)m * nL + eb + q];
     __syncthreads();
     T cf[NQ];
-    to_gauss<T, NP, NQ>(s_src, s_t1, sI, a, b, cf);
+    to_gauss<T, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, cf);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
-      ch0[c] = fma(G[(0 * 3 + m) * NQ3 + c * NQ2], cf[c], ch0[c]);
-      ch1[c] = fma(G[(1 * 3 + m) * NQ3 + c * NQ2], cf[c], ch1[c]);
-      ch2[c] = fma(G[(2 * 3 + m) * NQ3 + c * NQ2], cf[c], ch2[c]);
-    }
-  }
-  if (WIND_SMEM) {
+      const int pt = pt0 + c * NQ2;
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) {
-      const int pt = (c * NQ + b) * NQ + a;
-      s_ch[pt] = ch0[c];
-      s_ch[NQ3 + pt] = ch1[c];
-      s_ch[2 * NQ3 + pt] = ch2[c];
+      for (int d = 0; d < 3; ++d) s_ch[d * NQ3 + pt] = fma(G[(d * 3 + m) * NQ3 + c * NQ2], cf[c], s_ch[d * NQ3 + pt]);
     }
   }
   // 3. every advected component
@@ -183,43 +240,51 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = uv[(size_t)comp * nL + eb + q];
     __syncthreads();
     T uf[NQ];
-    to_gauss<T, NP, NQ>(s_src, s_t1, sI, a, b, uf);
+    to_gauss<T, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, uf);
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) s_U[(c * NQ + b) * NQ + a] = uf[c];
-    __syncthreads();
+    for (int c = 0; c < NQ; ++c) s_U[c * PS + b * RS + a] = uf[c];
     T conv[NQ];
     {
-      T da[NQ], db[NQ];   // rows a and b of the Gauss derivative matrix
+      T ut[NQ];
+      eo_deriv<T, NP>(P, uf, ut);   // t-derivative along this thread's line
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) {
-        da[m] = sD[a * NQ + m];
-        db[m] = sD[b * NQ + m];
-      }
-#pragma unroll
-      for (int c = 0; c < NQ; ++c) {
-        T ur = T(0), us = T(0), ut = T(0);
-#pragma unroll
-        for (int m = 0; m < NQ; ++m) {
-          ur = fma(da[m], s_U[(c * NQ + b) * NQ + m], ur);
-          us = fma(db[m], s_U[(c * NQ + m) * NQ + a], us);
-          ut = fma(sD[c * NQ + m], uf[m], ut);
-        }
-        if (WIND_SMEM) {
-          const int pt = (c * NQ + b) * NQ + a;
-          conv[c] = s_ch[pt] * ur + s_ch[NQ3 + pt] * us + s_ch[2 * NQ3 + pt] * ut;
-        } else {
-          conv[c] = ch0[c] * ur + ch1[c] * us + ch2[c] * ut;
-        }
-      }
+      for (int c = 0; c < NQ; ++c) conv[c] = s_ch[2 * NQ3 + pt0 + c * NQ2] * ut[c];
     }
-    // back to the GLL points: t-pass from registers into v2[k][b][a] (s_U reused)
     __syncthreads();
+    // r-derivative on the line (plane c = b, row j = a) -> s_R
+    {
+      T v[NQ], o[NQ];
+      const int rb = a, rc = b;
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) v[m] = s_U[rc * PS + rb * RS + m];
+      eo_deriv<T, NP>(P, v, o);
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) s_R[rc * PS + rb * RS + m] = o[m];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) conv[c] = fma(s_ch[pt0 + c * NQ2], s_R[c * PS + b * RS + a], conv[c]);
+    __syncthreads();
+    // s-derivative on the column (plane c = b, column i = a) -> s_R
+    {
+      T v[NQ], o[NQ];
+      const int sa = a, sc = b;
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) v[m] = s_U[sc * PS + m * RS + sa];
+      eo_deriv<T, NP>(P, v, o);
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) s_R[sc * PS + m * RS + sa] = o[m];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) conv[c] = fma(s_ch[NQ3 + pt0 + c * NQ2], s_R[c * PS + b * RS + a], conv[c]);
+    // back to the GLL points: t-pass from registers into v2[k][b][a] (s_U reused)
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NQ; ++c) acc = fma(sI[c * NP + k], conv[c], acc);
-      s_U[(k * NQ + b) * NQ + a] = acc;
+      for (int c = 0; c < NQ; ++c) acc = fma(P.Im[c * NP + k], conv[c], acc);
+      s_U[k * PS + b * RS + a] = acc;
     }
     __syncthreads();
     // s-pass: v1[k][j][a] = sum_b I[b][j] v2[k][b][a] (threads with b < NP own j = b)
@@ -231,7 +296,7 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
       for (int k = 0; k < NP; ++k) {
         T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc = fma(cb[q], s_U[(k * NQ + q) * NQ + a], acc);
+        for (int q = 0; q < NQ; ++q) acc = fma(cb[q], s_U[k * PS + q * RS + a], acc);
         s_t1[(k * NP + b) * NQ + a] = acc;
       }
     }
@@ -279,7 +344,7 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = X[m][eb + q] - x0;
     __syncthreads();
     double line[NQ];
-    to_gauss<double, NP, NQ>(s_src, s_t1, sI, a, b, line);
+    to_gauss<double, NP, NQ>(s_src, s_t1, sI, sI, a, b, line);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_X[(c * NQ + b) * NQ + a] = line[c];
     __syncthreads();
@@ -342,9 +407,29 @@ int cub_geom_launch(const Level& L, const double* Im, const double* Dq, const do
 }
 
 template <typename T, int NP>
-int advect_launch(const Level& L, const T* c, const T* u, T* w, int ncomp, const T* Gq, const T* Im,
-                  const T* Dq, cudaStream_t s) {
-  k_advect<T, NP><<<L.E, AdvShape<NP>::T, 0, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w);
+int advect_launch(const Level& L, const AdvData& A, const T* c, const T* u, T* w, int ncomp, const T* Gq,
+                  const T* Im, const T* Dq, cudaStream_t s) {
+  constexpr int NQ = nq_of(NP), H = NQ / 2, N = NQ - 1;
+  AdvOps<T, NP> P{};
+  for (int q = 0; q < NQ * NP; ++q) P.Im[q] = (T)A.hIm[q];
+  auto d = [&](int r, int q) { return A.hDq[r * NQ + q]; };
+  for (int r = 0; r < H; ++r)
+    for (int q = 0; q < H; ++q) {
+      P.ep[r * H + q] = (T)(0.5 * (d(r, q) + d(r, N - q)));
+      P.op[r * H + q] = (T)(0.5 * (d(r, q) - d(r, N - q)));
+    }
+  if (NQ % 2 == 1)
+    for (int r = 0; r < H; ++r) {
+      P.mc[r] = (T)d(r, H);
+      P.mr[r] = (T)d(H, r);
+    }
+  constexpr size_t smem = advect_smem<T, NP>();
+  static bool attr = false;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(k_advect<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  k_advect<T, NP><<<L.E, AdvShape<NP>::T, smem, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w, P);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
@@ -371,6 +456,8 @@ int advect_build(Ctx& C, cudaStream_t s) {
   std::vector<float> Im32(Im.begin(), Im.end()), Dq32(Dq.begin(), Dq.end());
   AdvData& A = C.adv;
   A.nq = NQ;
+  for (size_t q = 0; q < Im.size(); ++q) A.hIm[q] = Im[q];
+  for (size_t q = 0; q < Dq.size(); ++q) A.hDq[q] = Dq[q];
   const size_t ng = (size_t)L.E * 9 * NQ * NQ * NQ;
   auto dm = [&](void** p, size_t bytes) -> int {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
@@ -438,26 +525,26 @@ int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, 
     const double *cc = (const double*)c, *uu = (const double*)u;
     double* ww = (double*)w;
     switch (L.NP) {
-      ADV_DISPATCH(3, (advect_launch<double, 3>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(4, (advect_launch<double, 4>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(5, (advect_launch<double, 5>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(6, (advect_launch<double, 6>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(7, (advect_launch<double, 7>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(8, (advect_launch<double, 8>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(9, (advect_launch<double, 9>(L, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(3, (advect_launch<double, 3>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(4, (advect_launch<double, 4>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(5, (advect_launch<double, 5>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(6, (advect_launch<double, 6>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(7, (advect_launch<double, 7>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(8, (advect_launch<double, 8>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(9, (advect_launch<double, 9>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
       default: break;
     }
   } else {
     const float *cc = (const float*)c, *uu = (const float*)u;
     float* ww = (float*)w;
     switch (L.NP) {
-      ADV_DISPATCH(3, (advect_launch<float, 3>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(4, (advect_launch<float, 4>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(5, (advect_launch<float, 5>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(6, (advect_launch<float, 6>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(7, (advect_launch<float, 7>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(8, (advect_launch<float, 8>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(9, (advect_launch<float, 9>(L, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(3, (advect_launch<float, 3>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(4, (advect_launch<float, 4>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(5, (advect_launch<float, 5>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(6, (advect_launch<float, 6>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(7, (advect_launch<float, 7>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(8, (advect_launch<float, 8>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(9, (advect_launch<float, 9>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
       default: break;
     }
   }

@@ -143,6 +143,8 @@ struct AdvData {
   float* Gq32 = nullptr;
   double *Im = nullptr, *Dq = nullptr, *wq = nullptr;   // GLL -> Gauss interpolation, Gauss derivative, weights
   float *Im32 = nullptr, *Dq32 = nullptr;
+  double hIm[14 * 9] = {0};   // host copies (nq <= 14, N + 1 <= 9)
+  double hDq[14 * 14] = {0};
 };
 
 struct Ctx {
