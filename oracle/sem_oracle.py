@@ -1151,6 +1151,36 @@ def advect_assembled(level: "Level", cub: Cubature, cL, ug):
     return q_scatter(advect_local(level, cub, cL, uL), level.node, level.n_G)
 
 
+def char_advance(level: "Level", cub: Cubature, c0L, c1L, w0, t0: float, t1: float, nsub: int):
+    """The hyperbolic subproblem of the characteristics scheme (Section 2.1, eq. hyp):
+    dw/dt = -M^-1 Q^T C(c(t)) Q w on [t0, t1] from w(t0) = w0, with the assembled
+    diagonal GLL mass M and the dealiased advection operator C, by nsub classical
+    Runge-Kutta steps (RK4). The wind is linear in time between its values c0 at t0
+    and c1 at t1 (c1 None: frozen). w0: list of global vectors (components)."""
+    minv = 1.0 / level.mass()
+    h = (t1 - t0) / nsub
+
+    def wind(t):
+        if c1L is None:
+            return c0L
+        th = (t - t0) / (t1 - t0)
+        return c0L + th * (c1L - c0L)
+
+    def f(t, w):
+        cL = wind(t)
+        return [-minv * advect_assembled(level, cub, cL, wc) for wc in w]
+
+    w = [np.array(wc, dtype=np.float64) for wc in w0]
+    for q in range(nsub):
+        t = t0 + q * h
+        k1 = f(t, w)
+        k2 = f(t + 0.5 * h, [wc + 0.5 * h * kc for wc, kc in zip(w, k1)])
+        k3 = f(t + 0.5 * h, [wc + 0.5 * h * kc for wc, kc in zip(w, k2)])
+        k4 = f(t + h, [wc + h * kc for wc, kc in zip(w, k3)])
+        w = [wc + (h / 6.0) * (a1 + 2.0 * a2 + 2.0 * a3 + a4) for wc, a1, a2, a3, a4 in zip(w, k1, k2, k3, k4)]
+    return w
+
+
 # ----------------------------------------------------------------------------
 # Adjoint gradient with respect to nodal h1
 # ----------------------------------------------------------------------------
