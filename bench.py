@@ -373,7 +373,13 @@ def advect_bench(ctx, u, nG, E, N, stream, pk, steps=(5, 50)):
         peak = pk["fp64_tflops"] if prec == "fp64" else FP32_TFLOPS
         out[prec] = {"ms": 1e3 * t, "GDOF_per_s": 3 * nG / t / 1e9, "tflops": fl, "alu_peak_tflops": peak,
                      "alu_frac": fl / peak, "achieved_gbs": byt, "hbm_frac": byt / pk["hbm_gbs"]}
-        del c, uu, w
+        # one RK4 substep of the characteristics subproblem (4 operator evaluations, wind linear in time)
+        c1 = c.flip(0).contiguous()
+        sub = lambda: ctx.char_advance(c, uu, 0.0, 1e-3, 1, c1=c1, prec=prec)
+        sub()
+        ts = time_events(sub, max(2, nstep // 4), stream) / max(2, nstep // 4)
+        out[prec]["char_substep_ms"] = 1e3 * ts
+        del c, c1, uu, w
     return out
 
 

@@ -295,6 +295,18 @@ int sem_solve_proj(sem_ctx* ctx, sem_proj* pj, const double* f_L, const sem_coef
 int sem_advect(sem_ctx* ctx, int prec, const void* c_L, const void* u_L, void* w_L, int ncomp, int flags,
                void* stream);
 
+/* The hyperbolic subproblem of the characteristics (semi-Lagrangian) scheme, Section 2.1
+ * eq. hyp: w_t + c . grad w = 0 on [t0, t1], advanced in place by nsub classical RK4 steps of
+ *   dw/dt = -M^-1 Q Q^T C(c(t)) w
+ * with the dealiased operator of sem_advect and the assembled diagonal GLL mass M
+ * (no boundary condition is imposed: winds tangent to the walls need none). The
+ * wind is linear in time between c0 (at t0) and c1 (at t1); c1 = NULL freezes it at c0.
+ * c0_L, c1_L: [3][nL]; w_L: ncomp L-vectors [ncomp][nL], continuous, updated in place
+ * (must not alias the winds). prec SEM_FP64 / SEM_FP32. Workspace (3 ncomp + 3
+ * L-vectors) and the inverse mass are allocated on first use and kept. */
+int sem_char_advance(sem_ctx* ctx, int prec, const void* c0_L, const void* c1_L, void* w_L, int ncomp, double t0,
+                     double t1, int nsub, void* stream);
+
 /* Adjoint gradient with respect to nodal h1 (no counterpart in the paper's
  * solver; built on eq. Ae): g_L = -sum_{m,m'} (D_m lam)(G_mm')(D_m' u) at every
  * local point, with G excluding h1. For L = loss(u(h1)), A lam = dL/du gives

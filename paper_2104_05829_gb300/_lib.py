@@ -86,6 +86,7 @@ SIGNATURES = {
     "sem_vcycle": (_I, [_P, _P, _P, _P]),
     "sem_asm_apply": (_I, [_P, _I, _I, _P, _P, _D, _D, _P]),
     "sem_advect": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
+    "sem_char_advance": (_I, [_P, _I, _P, _P, _P, _I, _D, _D, _I, _P]),
     "sem_get_lmax": (_I, [_P, _P, _I]),
     "sem_solve": (_I, [_P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),
     "sem_solve_proj": (_I, [_P, _P, _P, C.POINTER(SemCoef), _D, _I, _I, _I, _I, _P, C.POINTER(SemInfo), _P]),

@@ -437,6 +437,58 @@ int advect_launch(const Level& L, const AdvData& A, const T* c, const T* u, T* w
 #define ADV_DISPATCH(NPV, CALL) \
   case NPV: return CALL;
 
+#define GRID_LOOP_ADV(l, n) \
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (n); l += (int64_t)gridDim.x * blockDim.x)
+
+inline unsigned vgrid_adv(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// m = B_L, the local GLL mass (component 6 of the geometric factors)
+__global__ void k_mass_local(int64_t n, int np3, const double* __restrict__ G, double* __restrict__ m) {
+  GRID_LOOP_ADV(l, n) {
+    const int64_t e = l / np3;
+    m[l] = G[(e * 7 + 6) * np3 + (l - e * np3)];
+  }
+}
+
+// minv = 1 / (QQ^T B) from the gathered mass in m (in place), FP64 and FP32 copies
+__global__ void k_minv(int64_t n, double* __restrict__ m, float* __restrict__ m32) {
+  GRID_LOOP_ADV(l, n) {
+    const double v = 1.0 / m[l];
+    m[l] = v;
+    m32[l] = (float)v;
+  }
+}
+
+// c(t) = c0 + th (c1 - c0) over the three wind components
+template <typename T>
+__global__ void k_wind(int64_t n, const T* __restrict__ c0, const T* __restrict__ c1, T th, T* __restrict__ c) {
+  GRID_LOOP_ADV(l, n) c[l] = c0[l] + th * (c1[l] - c0[l]);
+}
+
+// One RK4 stage on ncomp components: k = -minv z (z = QQ^T C w_stage);
+// mode 0: acc = k, ws = w + cw k; mode 1: acc += 2k, ws = w + cw k; mode 2: w += cw (acc + k).
+template <typename T>
+__global__ void k_rk_stage(int64_t n, int64_t nL, const T* __restrict__ z, const T* __restrict__ minv,
+                           T* __restrict__ w, T* __restrict__ ws, T* __restrict__ acc, T cw, int mode) {
+  GRID_LOOP_ADV(q, n) {
+    const T k = -minv[q % nL] * z[q];
+    if (mode == 0) {
+      acc[q] = k;
+      ws[q] = w[q] + cw * k;
+    } else if (mode == 1) {
+      acc[q] += T(2) * k;
+      ws[q] = w[q] + cw * k;
+    } else {
+      w[q] += cw * (acc[q] + k);
+    }
+  }
+}
+
 }  // namespace
 
 // Build the cubature data of level 0 (Gauss rule, interpolation and derivative
@@ -512,7 +564,7 @@ int advect_build(Ctx& C, cudaStream_t s) {
 }
 
 void advect_free(AdvData& A) {
-  void* ptrs[] = {A.Gq, A.Gq32, A.Im, A.Dq, A.wq, A.Im32, A.Dq32};
+  void* ptrs[] = {A.Gq, A.Gq32, A.Im, A.Dq, A.wq, A.Im32, A.Dq32, A.minv, A.minv32, A.ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   A = AdvData();
@@ -550,6 +602,86 @@ int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, 
   }
   set_detail("the dealiased advection operator is compiled for 2 <= N <= 8");
   return SEM_EINVAL;
+}
+
+// RK4 substeps of dw/dt = -M^-1 QQ^T C(c(t)) w (the hyperbolic subproblem of the
+// characteristics scheme, Section 2.1 eq. hyp): c(t) linear between c0 at t0 and
+// c1 at t1 (c1 null: frozen), nsub classical Runge-Kutta steps, w in place.
+int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int ncomp, double t0, double t1,
+                 int nsub, cudaStream_t s) {
+  const Level& L = C.lev[0];
+  AdvData& A = C.adv;
+  const int64_t nL = L.nL, n = (int64_t)ncomp * nL;
+  const size_t esz = prec == SEM_FP64 ? 8 : 4;
+  if (!A.minv) {
+    if (cudaMalloc(&A.minv, nL * 8) != cudaSuccess || cudaMalloc(&A.minv32, nL * 4) != cudaSuccess) {
+      cudaGetLastError();
+      set_detail("cudaMalloc of the inverse mass failed");
+      return SEM_ENOMEM;
+    }
+    k_mass_local<<<vgrid_adv(nL), 256, 0, s>>>(nL, L.NP * L.NP * L.NP, L.G, A.minv);
+    SEM_LAUNCH_CHECK();
+    SEM_TRY(gs_apply(L, SEM_FP64, A.minv, false, s));
+    k_minv<<<vgrid_adv(nL), 256, 0, s>>>(nL, A.minv, A.minv32);
+    SEM_LAUNCH_CHECK();
+  }
+  const size_t need = (3 * (size_t)n + 3 * (size_t)nL) * esz;
+  if (A.ws_bytes < need) {
+    if (A.ws) cudaFree(A.ws);
+    A.ws = nullptr;
+    A.ws_bytes = 0;
+    if (cudaMalloc(&A.ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      set_detail("cudaMalloc of %zu bytes failed (characteristics workspace)", need);
+      return SEM_ENOMEM;
+    }
+    A.ws_bytes = need;
+  }
+  char* base = static_cast<char*>(A.ws);
+  void* zb = base;                       // QQ^T C w_stage
+  void* wsb = base + n * esz;            // w_stage
+  void* accb = base + 2 * n * esz;       // sum of the weighted stages
+  void* cb = base + 3 * n * esz;         // c(t)
+  const double h = (t1 - t0) / nsub;
+  auto wind = [&](double t) -> const void* {
+    if (!c1) return c0;
+    const double th = (t - t0) / (t1 - t0);
+    if (prec == SEM_FP64)
+      k_wind<double><<<vgrid_adv(3 * nL), 256, 0, s>>>(3 * nL, (const double*)c0, (const double*)c1, th, (double*)cb);
+    else
+      k_wind<float><<<vgrid_adv(3 * nL), 256, 0, s>>>(3 * nL, (const float*)c0, (const float*)c1, (float)th,
+                                                     (float*)cb);
+    return cb;
+  };
+  auto eval = [&](double t, const void* win) -> int {   // z = QQ^T C(c(t)) win
+    const void* c = wind(t);
+    SEM_LAUNCH_CHECK();
+    SEM_TRY(advect_apply(C, prec, c, win, zb, ncomp, s));
+    for (int q = 0; q < ncomp; ++q) SEM_TRY(gs_apply(L, prec, static_cast<char*>(zb) + q * nL * esz, false, s));
+    return SEM_OK;
+  };
+  auto stage = [&](double cw, int mode) -> int {
+    if (prec == SEM_FP64)
+      k_rk_stage<double><<<vgrid_adv(n), 256, 0, s>>>(n, nL, (const double*)zb, A.minv, (double*)w, (double*)wsb,
+                                                      (double*)accb, cw, mode);
+    else
+      k_rk_stage<float><<<vgrid_adv(n), 256, 0, s>>>(n, nL, (const float*)zb, A.minv32, (float*)w, (float*)wsb,
+                                                     (float*)accb, (float)cw, mode);
+    SEM_LAUNCH_CHECK();
+    return SEM_OK;
+  };
+  for (int q = 0; q < nsub; ++q) {
+    const double t = t0 + q * h;
+    SEM_TRY(eval(t, w));
+    SEM_TRY(stage(0.5 * h, 0));
+    SEM_TRY(eval(t + 0.5 * h, wsb));
+    SEM_TRY(stage(0.5 * h, 1));
+    SEM_TRY(eval(t + 0.5 * h, wsb));
+    SEM_TRY(stage(h, 1));
+    SEM_TRY(eval(t + h, wsb));
+    SEM_TRY(stage(h / 6.0, 2));
+  }
+  return SEM_OK;
 }
 
 }  // namespace sem

@@ -145,6 +145,11 @@ struct AdvData {
   float *Im32 = nullptr, *Dq32 = nullptr;
   double hIm[14 * 9] = {0};   // host copies (nq <= 14, N + 1 <= 9)
   double hDq[14 * 14] = {0};
+  // characteristics substeps: inverse assembled mass and RK workspace (allocated on first use)
+  double* minv = nullptr;     // [nL] 1 / (QQ^T B_L)
+  float* minv32 = nullptr;
+  void* ws = nullptr;         // bytes: 3 stage arrays of ncomp L-vectors + one wind (3 L-vectors)
+  size_t ws_bytes = 0;
 };
 
 struct Ctx {
@@ -251,6 +256,8 @@ int arnoldi_lmax_asm(Ctx& C, int l, double h1, double h2, const double* v0, int 
 int advect_build(Ctx& C, cudaStream_t s);
 void advect_free(AdvData& A);
 int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s);
+int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int ncomp, double t0, double t1,
+                 int nsub, cudaStream_t s);
 
 // ---- proj.cu: projection of successive right-hand sides
 struct Proj;

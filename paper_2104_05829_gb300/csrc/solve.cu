@@ -511,6 +511,20 @@ int sem_advect(sem_ctx* h, int prec, const void* c, const void* u, void* w, int 
   return SEM_OK;
 }
 
+int sem_char_advance(sem_ctx* h, int prec, const void* c0, const void* c1, void* w, int ncomp, double t0, double t1,
+                     int nsub, void* stream) {
+  Ctx* C = ctx_of(h);
+  SEM_TRY(check_level(C, 0));
+  if (!c0 || !w || w == c0 || (c1 && w == c1) || ncomp < 1 || nsub < 1 || !(t1 != t0) ||
+      (prec != SEM_FP64 && prec != SEM_FP32)) {
+    set_detail("sem_char_advance: NULL or aliased vector, ncomp or nsub < 1, t1 == t0, or precision other than FP64/FP32");
+    return SEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SEM_TRY(advect_build(*C, s));
+  return char_advance(*C, prec, c0, c1, w, ncomp, t0, t1, nsub, s);
+}
+
 int sem_vcycle(sem_ctx* h, const double* r, double* z, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));

@@ -231,6 +231,18 @@ class SemContext:
                 "sem_advect")
         return w.reshape(-1) if squeeze else w
 
+    def char_advance(self, c0, w, t0, t1, nsub, c1=None, prec="fp64", stream=None):
+        """RK4 substeps of w_t + c . grad w = 0 on [t0, t1] in place (sem_char_advance).
+        c0, c1: (3, nL) winds at t0 and t1 (c1 None: frozen); w: (ncomp, nL) or (nL,)."""
+        dt = torch.float64 if _PREC[prec] in _F64 else torch.float32
+        w2 = w.reshape(-1, self.nL)
+        ncomp = w2.shape[0]
+        L.check(self._lib.sem_char_advance(self._h, _PREC[prec], _dev(c0, dt, 3 * self.nL, "c0"),
+                                           _dev(c1, dt, 3 * self.nL, "c1") if c1 is not None else None,
+                                           _dev(w2, dt, ncomp * self.nL, "w"), ncomp, float(t0), float(t1),
+                                           int(nsub), _stream(stream)), "sem_char_advance")
+        return w
+
     def vcycle(self, r, z=None, stream=None):
         z = torch.empty_like(r) if z is None else z
         L.check(self._lib.sem_vcycle(self._h, _dev(r, torch.float64, self.nL, "r"),
