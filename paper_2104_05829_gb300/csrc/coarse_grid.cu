@@ -134,14 +134,26 @@ __device__ void block_partial(T (&v)[NS], double* part) {
 }
 
 // Totals of the block partials, identical in every block (warp 0 reads them all
-// in a fixed lane-strided order and reduces in a fixed shuffle tree).
+// in a fixed lane-strided order and reduces in a fixed shuffle tree). The loads of
+// a lane are issued eight at a time before they are added (in the same order).
 template <int NS>
 __device__ void grid_totals(const double* part, double* tot) {
   if (threadIdx.x < 32) {
+    const unsigned G = gridDim.x;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       double t = 0;
-      for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) t += __ldcg(part + s * gridDim.x + q);
+      for (unsigned q0 = threadIdx.x; q0 < G; q0 += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const unsigned q = q0 + 32 * k;
+          v[k] = q < G ? __ldcg(part + s * G + q) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (q0 + 32 * k < G) t += v[k];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (threadIdx.x == 0) tot[s] = t;
@@ -278,14 +290,31 @@ __global__ void __launch_bounds__(GT_THREADS) k_coarse_grid(GridArgs a, Mat64 D)
     grid_barrier(a.bar, a.bar + gridDim.x, a.err, epoch);
     // gather-scatter of shared / Dirichlet nodes, with (w, u) at their owner copies
     for (int sg = threadIdx.x; sg < ns; sg += GT_THREADS) {
-      const int bgn = g_off[sg], end = g_off[sg + 1];
+      const int bgn = g_off[sg], end = g_off[sg + 1], m = end - bgn;
       if (g_dir[sg]) {
         for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], T(0));
+      } else if (m <= 8) {
+        // every load of the node's copies (and of u at its owner) in flight at once
+        int id[8];
+        T v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) id[t] = t < m ? g_idx[bgn + t] : 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = t < m ? __ldcg(w + id[t]) : T(0);
+        const T uo = __ldcg(pg + id[0]);
+        T sum = v[0];
+#pragma unroll
+        for (int t = 1; t < 8; ++t)
+          if (t < m) sum += v[t];
+        if (m > 1)
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (t < m) __stcg(w + id[t], sum);
+        acc[2] = fma(uo, sum, acc[2]);
       } else {
         T sum = __ldcg(w + g_idx[bgn]);
         for (int q = bgn + 1; q < end; ++q) sum += __ldcg(w + g_idx[q]);
-        if (end - bgn > 1)
-          for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], sum);
+        for (int q = bgn; q < end; ++q) __stcg(w + g_idx[q], sum);
         acc[2] = fma(__ldcg(pg + g_idx[bgn]), sum, acc[2]);
       }
     }
