@@ -429,7 +429,7 @@ def main():
     ap.add_argument("--no-proj", action="store_true", help="skip the successive-RHS projection sequence")
     ap.add_argument("--no-advect", action="store_true", help="skip the dealiased advection timing")
     ap.add_argument("--coarse-tol", type=float, default=None, help="coarse Jacobi-PCG tolerance (default 1e-2)")
-    ap.add_argument("--coarse-mode", default="auto", choices=["auto", "cluster", "grid", "kernels"],
+    ap.add_argument("--coarse-mode", default="auto", choices=["auto", "pipe", "cluster", "grid", "kernels"],
                     help="execution of the coarse Jacobi-PCG (same algorithm)")
     ap.add_argument("--proj-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")

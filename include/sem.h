@@ -71,10 +71,12 @@ extern "C" {
 #define SEM_SMOOTH_ASM 1     /* Chebyshev-accelerated overlapping Schwarz with FDM local solves (CHEBY-ASM) */
 
 /* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in all of them */
-#define SEM_COARSE_AUTO 0     /* the first that applies of GRID, CLUSTER, KERNELS */
+#define SEM_COARSE_AUTO 0     /* the first that applies of PIPE, GRID, CLUSTER, KERNELS */
 #define SEM_COARSE_CLUSTER 1  /* FP32/BF16 V-cycles: one launch on one cluster, problem held on chip; else KERNELS */
 #define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches */
 #define SEM_COARSE_GRID 3     /* one cooperative launch over the whole GPU when it fits; else KERNELS */
+#define SEM_COARSE_PIPE 4     /* pipelined PCG on one sub-domain per SM, one cooperative launch with one
+                                 grid-wide synchronisation per iteration, when it fits; else KERNELS */
 
 /* sem_solve preconditioners and flags */
 #define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */
@@ -358,6 +360,30 @@ int sem_get_geom_lowp(const sem_ctx* ctx, int level, int prec, void* G);
 int sem_get_coords(const sem_ctx* ctx, int level, double* x, double* y, double* z, int64_t* gid);
 /* GLL nodes, weights and D_hat (row-major, D[a*(N+1)+b] = h_b'(xi_a)) for order N. */
 int sem_gll(int N, double* xi, double* rho, double* D);
+
+/* Sub-domain partition of an order-1 level as the pipelined coarse solve (SEM_COARSE_PIPE)
+ * builds it: HOST-only (no GPU), for inspection and tests. Direct-stiffness summation
+ * QQ^T (Section 3.2) becomes, per sub-domain, a sum over every copy of each node it holds.
+ * In: E elements of 8 points (point l = 8e + i + 2j + 4k); node[8E] the unique node of each
+ * point, 0 <= node < nG; dmask[8E] 1 at Dirichlet nodes; owner[8E] 1 at the copy of each
+ * non-Dirichlet node that counts in dot products; x, y, z[8E] coordinates (element centroids
+ * are split by recursive coordinate bisection); nblocks sub-domains, 1 <= nblocks <= E.
+ * Out, caller-allocated: el_off[nblocks+1] and el[E]: elements grouped by sub-domain, ascending
+ * within one. p2n[8E]: for the points in el order, the point's sub-domain node, with bit 31 set
+ * when that node has copies in other sub-domains. nd_off[nblocks+1]: offsets of each
+ * sub-domain's nodes, numbered by first appearance. nd_src[cap_nodes]: one local point of each
+ * node. nd_fl[cap_nodes]: bit 0 set where the sub-domain holds the owner copy, bit 1 at
+ * Dirichlet nodes. cp_off[cap_nodes+1] and cp[cap_copies]: every copy of each node in
+ * ascending local index; an entry >= 0 is a point of the sub-domain (offset from its first
+ * point in el order), an entry < 0 is -(local point + 1) in another sub-domain.
+ * counts[5]: nodes, copies, then the largest sub-domain's elements, nodes and copies.
+ * Errors: SEM_EINVAL for a NULL pointer, bad sizes or node numbers, or capacities that are
+ * too small (counts is filled in that case). */
+int sem_coarse_partition(int32_t E, int64_t nG, const int32_t* node, const uint8_t* dmask,
+                         const uint8_t* owner, const double* x, const double* y, const double* z,
+                         int32_t nblocks, int64_t cap_nodes, int64_t cap_copies, int32_t* el_off,
+                         int32_t* el, int32_t* p2n, int32_t* nd_off, int32_t* nd_src, uint8_t* nd_fl,
+                         int32_t* cp_off, int32_t* cp, int64_t* counts);
 
 #ifdef __cplusplus
 }

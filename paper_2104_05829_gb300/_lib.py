@@ -27,7 +27,7 @@ SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
 SEM_ADV_LOCAL, SEM_ADV_ASSEMBLE = 0, 1
-SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS, SEM_COARSE_GRID = 0, 1, 2, 3
+SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS, SEM_COARSE_GRID, SEM_COARSE_PIPE = 0, 1, 2, 3, 4
 
 
 class SemMesh(C.Structure):
@@ -107,6 +107,8 @@ SIGNATURES = {
     "sem_get_geom_lowp": (_I, [_P, _I, _I, _P]),
     "sem_get_coords": (_I, [_P, _I, _P, _P, _P, _P]),
     "sem_gll": (_I, [_I, _P, _P, _P]),
+    "sem_coarse_partition": (_I, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_int64,
+                                  C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None

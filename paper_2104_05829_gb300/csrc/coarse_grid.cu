@@ -28,6 +28,7 @@
 #include <algorithm>
 
 #include "sem_internal.cuh"
+#include "spin.cuh"
 
 namespace sem {
 
@@ -66,22 +67,6 @@ struct GridArgs {
 __device__ __forceinline__ double fval(double v) { return v; }
 __device__ __forceinline__ float fval(float v) { return v; }
 __device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// Wait until *v >= target, at most about a second of SM clock (2^31 cycles); then
-// raise the error flag. The flag is re-read every 64 polls.
-__device__ __forceinline__ void wait_at_least(const unsigned* v, unsigned target, int* err) {
-  const long long t0 = clock64();
-  unsigned polls = 0;
-  while (*(const volatile unsigned*)v < target) {
-    if ((++polls & 63u) == 0) {
-      if (*(volatile int*)err != 0) return;   // another block gave up: stop waiting
-      if (clock64() - t0 > (1ll << 31)) {
-        atomicExch(err, 1);
-        return;
-      }
-    }
-  }
-}
 
 // Grid barrier without a contended counter: every block publishes the barrier's
 // epoch in its own flag; block 0's threads wait for all flags in parallel and

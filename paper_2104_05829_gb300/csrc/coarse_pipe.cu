@@ -1,0 +1,690 @@
+// Coarsest-level Jacobi-PCG (order 1) as pipelined PCG on sub-domains, in one
+// cooperative launch with one grid-wide synchronisation per iteration.
+//
+// The order-1 elements are split into one sub-domain per block by recursive
+// coordinate bisection of their centroids (host, once per level). A block keeps
+// the assembled Krylov vectors of every node its elements touch in registers
+// (a node on a sub-domain interface is held by every block that touches it,
+// with identical bits), and its elements' geometric factors, point-to-node map
+// and node copy lists in shared memory. The direct-stiffness sum QQ^T of an
+// operator output is a gather: every block sums, for each of its nodes, all
+// copies of the node in canonical order (ascending local index), its own copies
+// from shared memory and the other blocks' from an exchange buffer that those
+// blocks publish before the synchronisation. Nothing is scattered into another
+// block, so one synchronisation per operator application suffices.
+//
+// The iteration is pipelined PCG (Ghysels and Vanroose, Parallel Computing
+// 2014) with the Jacobi preconditioner: the dot products of an iteration need
+// only vectors that exist before its operator application, so their block
+// partials travel with the same synchronisation. In exact arithmetic the
+// iterates are those of Jacobi-PCG.
+//   r = b, u = D^-1 r, w = A u (one extra synchronisation); for i = 0, 1, ...
+//     gamma = (r, u), delta = (w, u), rr = (r, r); m = D^-1 w; n = A m
+//     stop if rr <= tol^2 (b, b) or i = maxit (x is the result)
+//     beta = gamma / gamma_old (0 at i = 0), alpha = gamma / (delta - beta gamma / alpha_old)
+//     z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
+//     x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
+// Dot products count each non-Dirichlet node once (in the block holding its
+// owner copy); block partials are summed in FP64, and every block adds all of
+// them in one fixed order, so all blocks take the same decisions.
+// Synchronisation: a block publishes an epoch in its own flag after its writes;
+// the first warp of every block waits for all flags. The exchange buffer and the
+// partials are double-buffered by epoch parity: no block can be more than one
+// synchronisation ahead of another. Waits are bounded (about a second of SM
+// clock); after a timeout every wait ends at once and the solve reports a
+// breakdown.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "sem_internal.cuh"
+#include "spin.cuh"
+
+namespace sem {
+
+namespace {
+
+constexpr int PT = 512;             // threads per block
+constexpr int PW = PT / 32;
+constexpr int NPC = 2;              // order 1
+constexpr int NPC3 = 8;
+constexpr int GF = 7 * NPC3;        // factor values per element
+constexpr int32_t NODE_MASK = 0x7fffffff;
+
+struct PipeArgs {
+  const void* G;                    // [E][7][8]
+  const void* b;
+  void* x;
+  const void* dinv;
+  void* xbuf;                       // [2][nL] in the arithmetic type
+  int64_t nL;
+  const int32_t* el_off;
+  const int32_t* el;
+  const int32_t* p2n;
+  const int32_t* nd_off;
+  const int32_t* nd_src;
+  const uint8_t* nd_fl;
+  const int32_t* cp_off;
+  const int32_t* cp;
+  int max_el, max_nd, max_cp;
+  double h1, h2, tol;
+  int maxit;
+  double* part;                     // [2][3][B]
+  unsigned* flags;                  // [B], zero before the launch
+  int* err;
+  double* sc;                       // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
+};
+
+__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
+
+// shared-memory layout of a block (the same offsets on host and device)
+struct PipeSmem {
+  size_t pt, m, el, p2n, cpo, cp, total;
+  template <typename T, typename GT, bool SMEM_G>
+  __host__ __device__ static PipeSmem make(int max_el, int max_nd, int max_cp) {
+    PipeSmem o{};
+    o.pt = SMEM_G ? al16((size_t)max_el * GF * sizeof(GT)) : 0;
+    o.m = o.pt + al16((size_t)max_el * NPC3 * sizeof(T));
+    o.el = o.m + al16((size_t)max_nd * sizeof(T));
+    o.p2n = o.el + al16((size_t)max_el * 4);
+    o.cpo = o.p2n + al16((size_t)max_el * NPC3 * 4);
+    o.cp = o.cpo + al16((size_t)(max_nd + 1) * 4);
+    o.total = o.cp + al16((size_t)max_cp * 4);
+    return o;
+  }
+};
+
+__device__ __forceinline__ double fval(double v) { return v; }
+__device__ __forceinline__ float fval(float v) { return v; }
+__device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// All blocks have written what they publish for this epoch once this returns.
+__device__ void sync_all(unsigned* flags, int* err, unsigned epoch) {
+  __syncthreads();
+  const bool live = *(volatile int*)err == 0;
+  if (threadIdx.x == 0 && live) {
+    __threadfence();
+    atomicExch(flags + blockIdx.x, epoch);
+  }
+  if (threadIdx.x < 32) {
+    if (live)
+      for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) wait_at_least(flags + q, epoch, err);
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <typename T, typename GT, int NPT, bool SMEM_G>
+__global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  const PipeSmem lay = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp);
+  GT* sG = reinterpret_cast<GT*>(s_raw);
+  T* s_pt = reinterpret_cast<T*>(s_raw + lay.pt);          // operator output per sub-domain point
+  T* s_m = reinterpret_cast<T*>(s_raw + lay.m);            // operator input per sub-domain node
+  int32_t* s_el = reinterpret_cast<int32_t*>(s_raw + lay.el);
+  int32_t* s_p2n = reinterpret_cast<int32_t*>(s_raw + lay.p2n);
+  int32_t* s_cpo = reinterpret_cast<int32_t*>(s_raw + lay.cpo);
+  int32_t* s_cp = reinterpret_cast<int32_t*>(s_raw + lay.cp);
+  __shared__ double s_red[PW][3];
+  __shared__ int s_flag;             // 0 go on, 1 converged, 2 breakdown, 3 iteration cap
+  __shared__ T s_al, s_be;
+  const int B = gridDim.x, bk = blockIdx.x;
+  const int el0 = a.el_off[bk], nel = a.el_off[bk + 1] - el0, npt = nel * NPC3;
+  const int nd0 = a.nd_off[bk], nnd = a.nd_off[bk + 1] - nd0;
+  const int cp0 = a.cp_off[nd0], ncp = a.cp_off[nd0 + nnd] - cp0;
+  const GT* G = static_cast<const GT*>(a.G);
+  const T* bv = static_cast<const T*>(a.b);
+  const T* dv = static_cast<const T*>(a.dinv);
+  T* xbuf = static_cast<T*>(a.xbuf);
+  for (int q = threadIdx.x; q < nel; q += PT) s_el[q] = a.el[el0 + q];
+  for (int q = threadIdx.x; q < npt; q += PT) s_p2n[q] = a.p2n[(int64_t)el0 * NPC3 + q];
+  for (int q = threadIdx.x; q <= nnd; q += PT) s_cpo[q] = a.cp_off[nd0 + q] - cp0;
+  for (int q = threadIdx.x; q < ncp; q += PT) s_cp[q] = a.cp[cp0 + q];
+  __syncthreads();
+  if (SMEM_G)
+    for (int q = threadIdx.x; q < nel * GF; q += PT) {
+      const int k = q / GF;
+      sG[q] = G[(int64_t)s_el[k] * GF + (q - k * GF)];
+    }
+  // element operator constants of this thread's point within its element
+  const int lq = threadIdx.x & 7;
+  const int i = lq & 1, j = (lq >> 1) & 1, k = lq >> 2;
+  const T d00 = (T)D.a[0], d01 = (T)D.a[1], d10 = (T)D.a[2], d11 = (T)D.a[3];
+  const T di_s = i ? d11 : d00, di_o = i ? d10 : d01;
+  const T dj_s = j ? d11 : d00, dj_o = j ? d10 : d01;
+  const T dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
+  const T ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;
+  const T h1 = (T)a.h1, h2 = (T)a.h2;
+  // node state (slot c: node threadIdx.x + c * PT of the sub-domain)
+  T x[NPT], r[NPT], u[NPT], w[NPT], z[NPT], qv[NPT], sv[NPT], p[NPT], di[NPT], mv[NPT];
+  unsigned own = 0, dir = 0, live = 0;
+#pragma unroll
+  for (int c = 0; c < NPT; ++c) {
+    const int jn = threadIdx.x + c * PT;
+    x[c] = r[c] = u[c] = w[c] = z[c] = qv[c] = sv[c] = p[c] = di[c] = mv[c] = T(0);
+    if (jn < nnd) {
+      live |= 1u << c;
+      const uint8_t fl = a.nd_fl[nd0 + jn];
+      const int32_t src = a.nd_src[nd0 + jn];
+      if (fl & 1) own |= 1u << c;
+      if (fl & 2) {
+        dir |= 1u << c;
+      } else {
+        di[c] = dv[src];
+        r[c] = bv[src];
+      }
+      u[c] = di[c] * r[c];
+    }
+  }
+  __syncthreads();   // factors staged
+
+  // s_pt = A_L s_m on the sub-domain's points; interface points also go to xb
+  auto apply = [&](T* xb) {
+    const int nch = (npt + PT - 1) / PT;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int bp = threadIdx.x + ch * PT;
+      const bool lv = bp < npt;
+      const int32_t pn = lv ? s_p2n[bp] : 0;
+      const T uu = lv ? s_m[pn & NODE_MASK] : T(0);
+      const T ur = di_s * uu + di_o * __shfl_xor_sync(0xffffffffu, uu, 1);
+      const T us = dj_s * uu + dj_o * __shfl_xor_sync(0xffffffffu, uu, 2);
+      const T ut = dk_s * uu + dk_o * __shfl_xor_sync(0xffffffffu, uu, 4);
+      T wr = T(0), ws = T(0), wt = T(0), bu = T(0);
+      if (lv) {
+        const GT* g = SMEM_G ? sG + (bp >> 3) * GF + lq : G + (int64_t)s_el[bp >> 3] * GF + lq;
+        const T g11 = (T)fval(g[0]), g12 = (T)fval(g[8]), g13 = (T)fval(g[16]);
+        const T g22 = (T)fval(g[24]), g23 = (T)fval(g[32]), g33 = (T)fval(g[40]);
+        wr = h1 * (g11 * ur + g12 * us + g13 * ut);
+        ws = h1 * (g12 * ur + g22 * us + g23 * ut);
+        wt = h1 * (g13 * ur + g23 * us + g33 * ut);
+        bu = h2 * (T)fval(g[48]) * uu;
+      }
+      T wv = bu + di_s * wr + ti_o * __shfl_xor_sync(0xffffffffu, wr, 1);
+      wv += dj_s * ws + tj_o * __shfl_xor_sync(0xffffffffu, ws, 2);
+      wv += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
+      if (lv) {
+        s_pt[bp] = wv;
+        if (pn < 0) __stcg(xb + (int64_t)s_el[bp >> 3] * NPC3 + lq, wv);
+      }
+    }
+  };
+  // assembled value of node slot c: every copy, in canonical order
+  auto gather = [&](int c, const T* xb) -> T {
+    const int jn = threadIdx.x + c * PT;
+    if (!((live >> c) & 1u) || ((dir >> c) & 1u)) return T(0);
+    const int q0 = s_cpo[jn], m = s_cpo[jn + 1] - q0;
+    if (m <= 8) {
+      T v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[t] = T(0);
+        if (t < m) {
+          const int32_t e = s_cp[q0 + t];
+          v[t] = e >= 0 ? s_pt[e] : __ldcg(xb + (-(int64_t)e - 1));
+        }
+      }
+      T sum = v[0];
+#pragma unroll
+      for (int t = 1; t < 8; ++t)
+        if (t < m) sum += v[t];
+      return sum;
+    }
+    T sum = T(0);
+    for (int t = 0; t < m; ++t) {
+      const int32_t e = s_cp[q0 + t];
+      const T v = e >= 0 ? s_pt[e] : __ldcg(xb + (-(int64_t)e - 1));
+      sum = t == 0 ? v : sum + v;
+    }
+    return sum;
+  };
+
+  unsigned epoch = 0;
+  // w = A u
+#pragma unroll
+  for (int c = 0; c < NPT; ++c)
+    if ((live >> c) & 1u) s_m[threadIdx.x + c * PT] = u[c];
+  __syncthreads();
+  apply(xbuf + (size_t)((epoch + 1) & 1u) * a.nL);
+  sync_all(a.flags, a.err, ++epoch);
+#pragma unroll
+  for (int c = 0; c < NPT; ++c) w[c] = gather(c, xbuf + (size_t)(epoch & 1u) * a.nL);
+
+  // scalar state, held by thread 0
+  double bb = 0, tol2 = 0, gam = 0, alpha_old = 0, rr = 0;
+  int flag = 0, it = 0;
+  for (int pass = 0;; ++pass) {
+    // gamma, delta, rr over owned nodes; m = D^-1 w
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < NPT; ++c) {
+      mv[c] = di[c] * w[c];
+      if ((live >> c) & 1u) s_m[threadIdx.x + c * PT] = mv[c];
+      if ((own >> c) & 1u) {
+        acc[0] = fma(r[c], u[c], acc[0]);
+        acc[1] = fma(w[c], u[c], acc[1]);
+        acc[2] = fma(r[c], r[c], acc[2]);
+      }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+      if (lane == 0) s_red[warp][t] = (double)acc[t];
+    }
+    __syncthreads();
+    const unsigned par = (epoch + 1) & 1u;
+    if (threadIdx.x < 3) {
+      double t = 0;
+      for (int q = 0; q < PW; ++q) t += s_red[q][threadIdx.x];
+      __stcg(a.part + (size_t)par * 3 * B + (size_t)threadIdx.x * B + bk, t);
+    }
+    apply(xbuf + (size_t)par * a.nL);
+    sync_all(a.flags, a.err, ++epoch);
+    // n = QQ^T of the published outputs; the totals of the partials
+    const T* xb = xbuf + (size_t)(epoch & 1u) * a.nL;
+    T nv[NPT];
+#pragma unroll
+    for (int c = 0; c < NPT; ++c) nv[c] = gather(c, xb);
+    if (threadIdx.x < 32) {
+      const double* pp = a.part + (size_t)(epoch & 1u) * 3 * B;
+      double tot[3];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        double v = 0;
+        for (int q = threadIdx.x; q < B; q += 32) v += __ldcg(pp + (size_t)t * B + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        tot[t] = v;
+      }
+      if (threadIdx.x == 0) {
+        const double gnew = tot[0], del = tot[1];
+        rr = tot[2];
+        if (pass == 0) {
+          bb = rr;
+          tol2 = a.tol * a.tol * bb;
+        }
+        it = pass;
+        int f = 0;
+        double alpha = 0, beta = 0;
+        if (*(volatile int*)a.err != 0 || !isfinite(rr)) f = 2;
+        else if (rr <= tol2) f = 1;
+        else if (pass >= a.maxit) f = 3;
+        else {
+          beta = pass == 0 ? 0.0 : gnew / gam;
+          const double den = pass == 0 ? del : del - beta * gnew / alpha_old;
+          alpha = gnew / den;
+          if (!(den > 0.0) || !(gnew > 0.0) || !isfinite(alpha)) f = 2;
+        }
+        gam = gnew;
+        alpha_old = alpha;
+        s_flag = f;
+        s_al = (T)alpha;
+        s_be = (T)beta;
+      }
+    }
+    __syncthreads();
+    flag = s_flag;
+    if (flag != 0) break;
+    const T al = s_al, be = s_be;
+#pragma unroll
+    for (int c = 0; c < NPT; ++c) {
+      z[c] = fma(be, z[c], nv[c]);
+      qv[c] = fma(be, qv[c], mv[c]);
+      sv[c] = fma(be, sv[c], w[c]);
+      p[c] = fma(be, p[c], u[c]);
+      x[c] = fma(al, p[c], x[c]);
+      r[c] = fma(-al, sv[c], r[c]);
+      u[c] = fma(-al, qv[c], u[c]);
+      w[c] = fma(-al, z[c], w[c]);
+    }
+  }
+  // x at every point of the sub-domain
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NPT; ++c)
+    if ((live >> c) & 1u) s_m[threadIdx.x + c * PT] = x[c];
+  __syncthreads();
+  T* xg = static_cast<T*>(a.x);
+  for (int bp = threadIdx.x; bp < npt; bp += PT)
+    xg[(int64_t)s_el[bp >> 3] * NPC3 + (bp & 7)] = s_m[s_p2n[bp] & NODE_MASK];
+  if (bk == 0 && threadIdx.x == 0) {
+    a.sc[S_ITER] = it;
+    a.sc[S_TOTAL] += it;
+    a.sc[S_RR] = rr;
+    a.sc[S_BB] = bb;
+    a.sc[S_BREAK] = flag == 2 ? 1 : 0;
+    a.sc[S_DONE] = 1;
+  }
+}
+
+// Recursive coordinate bisection: el[0..n) goes to parts part0 .. part0 + parts - 1,
+// part sizes within one of each other; each part's elements end up ascending.
+void rcb(int32_t* el, int n, int parts, int part0, int32_t base, const std::vector<double>* c,
+         std::vector<int32_t>& el_off) {
+  if (parts == 1) {
+    el_off[part0] = base;
+    std::sort(el, el + n);
+    return;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int q = 0; q < n; ++q)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c[d][el[q]]);
+      hi[d] = std::max(hi[d], c[d][el[q]]);
+    }
+  int ax = 0;
+  for (int d = 1; d < 3; ++d)
+    if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+  const std::vector<double>& cc = c[ax];
+  const int p1 = parts / 2;
+  const int n1 = (int)((int64_t)n * p1 / parts);
+  std::nth_element(el, el + n1, el + n,
+                   [&](int32_t x, int32_t y) { return cc[x] < cc[y] || (cc[x] == cc[y] && x < y); });
+  rcb(el, n1, p1, part0, base, c, el_off);
+  rcb(el + n1, n - n1, parts - p1, part0 + p1, base + n1, c, el_off);
+}
+
+template <typename V>
+int upload(V** dst, const std::vector<V>& src, cudaStream_t s) {
+  if (cudaMalloc((void**)dst, src.size() * sizeof(V) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    set_detail("cudaMalloc failed (sub-domain coarse solve)");
+    return SEM_ENOMEM;
+  }
+  if (!src.empty()) SEM_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, s));
+  return SEM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Sub-domain structures of an order-1 level, built on the host.
+struct PipeHost {
+  std::vector<int32_t> el_off, el, p2n, nd_off, nd_src, cp_off, cp;
+  std::vector<uint8_t> nd_fl;
+  int max_el = 0, max_nd = 0, max_cp = 0;
+};
+
+// Partition E order-1 elements (points 8e .. 8e + 7, canonical node node[l] < nG)
+// into B sub-domains and list, per sub-domain, its nodes (in order of first
+// appearance), their copies in canonical order and the published points.
+int pipe_partition(int E, int64_t nG, const int32_t* node, const uint8_t* dmask, const uint8_t* owner,
+                   const double* x, const double* y, const double* z, int B, PipeHost* h) {
+  const int64_t nL = (int64_t)E * NPC3;
+  if (E < 1 || B < 1 || B > E || nL >= (int64_t)INT32_MAX / 2) {
+    set_detail("sub-domain partition: E = %d, B = %d", E, B);
+    return SEM_EINVAL;
+  }
+  for (int64_t l = 0; l < nL; ++l)
+    if (node[l] < 0 || node[l] >= nG) {
+      set_detail("sub-domain partition: node index out of range at point %lld", (long long)l);
+      return SEM_EINVAL;
+    }
+  const double* xyz[3] = {x, y, z};
+  std::vector<double> cen[3];
+  for (int d = 0; d < 3; ++d) {
+    cen[d].assign(E, 0.0);
+    for (int e = 0; e < E; ++e) {
+      double t = 0;
+      for (int q = 0; q < NPC3; ++q) t += xyz[d][(int64_t)e * NPC3 + q];
+      cen[d][e] = t / NPC3;
+    }
+  }
+  h->el.resize(E);
+  h->el_off.assign(B + 1, 0);
+  std::iota(h->el.begin(), h->el.end(), 0);
+  rcb(h->el.data(), E, B, 0, 0, cen, h->el_off);
+  h->el_off[B] = E;
+  const std::vector<int32_t>& el = h->el;
+  const std::vector<int32_t>& el_off = h->el_off;
+  std::vector<int32_t> blk(E), pos(E);
+  for (int b = 0; b < B; ++b)
+    for (int q = el_off[b]; q < el_off[b + 1]; ++q) {
+      blk[el[q]] = b;
+      pos[el[q]] = q - el_off[b];
+    }
+  // copies of every node, ascending local index
+  std::vector<int64_t> hoff(nG + 1, 0);
+  for (int64_t l = 0; l < nL; ++l) ++hoff[node[l] + 1];
+  for (int64_t g = 0; g < nG; ++g) hoff[g + 1] += hoff[g];
+  std::vector<int32_t> hidx(nL);
+  {
+    std::vector<int64_t> fill(hoff.begin(), hoff.end() - 1);
+    for (int64_t l = 0; l < nL; ++l) hidx[fill[node[l]]++] = (int32_t)l;
+  }
+  h->p2n.assign(nL, 0);
+  h->nd_off.assign(B + 1, 0);
+  h->nd_src.clear();
+  h->nd_fl.clear();
+  h->cp.clear();
+  h->cp_off.assign(1, 0);
+  std::vector<int32_t> local(nG, -1), list;
+  for (int b = 0; b < B; ++b) {
+    h->nd_off[b] = (int32_t)h->nd_src.size();
+    const int64_t pbase = (int64_t)el_off[b] * NPC3;
+    list.clear();
+    for (int q = el_off[b]; q < el_off[b + 1]; ++q)
+      for (int t = 0; t < NPC3; ++t) {
+        const int32_t g = node[(int64_t)el[q] * NPC3 + t];
+        if (local[g] < 0) {
+          local[g] = (int32_t)list.size();
+          list.push_back(g);
+        }
+        h->p2n[pbase + (int64_t)(q - el_off[b]) * NPC3 + t] = local[g];
+      }
+    const size_t cp_b = h->cp.size();
+    for (int32_t g : list) {
+      int32_t src = -1;
+      uint8_t fl = 0;
+      bool remote = false;
+      const size_t first = h->cp.size();
+      for (int64_t o = hoff[g]; o < hoff[g + 1]; ++o) {
+        const int32_t l = hidx[o];
+        const int32_t e = l / NPC3;
+        if (blk[e] == b) {
+          h->cp.push_back(pos[e] * NPC3 + l % NPC3);
+          if (src < 0) src = l;
+          if (owner[l]) fl |= 1;
+        } else {
+          h->cp.push_back(-(l + 1));
+          remote = true;
+        }
+      }
+      if (dmask[src]) fl |= 2;
+      if (remote)
+        for (size_t o = first; o < h->cp.size(); ++o)
+          if (h->cp[o] >= 0) h->p2n[pbase + h->cp[o]] |= (int32_t)0x80000000u;
+      h->nd_src.push_back(src);
+      h->nd_fl.push_back(fl);
+      h->cp_off.push_back((int32_t)h->cp.size());
+      if (h->cp.size() >= (size_t)INT32_MAX / 2) {
+        set_detail("sub-domain partition: too many copy entries");
+        return SEM_EINVAL;
+      }
+    }
+    for (int32_t g : list) local[g] = -1;
+    h->max_el = std::max(h->max_el, el_off[b + 1] - el_off[b]);
+    h->max_nd = std::max(h->max_nd, (int)list.size());
+    h->max_cp = std::max(h->max_cp, (int)(h->cp.size() - cp_b));
+  }
+  h->nd_off[B] = (int32_t)h->nd_src.size();
+  return SEM_OK;
+}
+
+}  // namespace
+
+// Sub-domains, node lists and copy lists of an order-1 level (synchronous, host
+// work O(nL)); leaves L.pp_blocks = -1 where the solve does not apply.
+int coarse_pipe_build(Level& L, cudaStream_t s) {
+  if (L.pp_blocks != 0) return SEM_OK;
+  L.pp_blocks = -1;
+  if (L.NP != NPC || L.E < 1 || L.nL >= (int64_t)INT32_MAX / 2) return SEM_OK;
+  int dev = 0, nsm = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t nL = L.nL;
+  std::vector<double> xyz[3];
+  for (auto& v : xyz) v.resize(nL);
+  std::vector<int32_t> node(nL);
+  std::vector<uint8_t> dmask(nL), owner(nL);
+  SEM_CUDA_TRY(cudaMemcpyAsync(xyz[0].data(), L.x, nL * 8, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(xyz[1].data(), L.y, nL * 8, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(xyz[2].data(), L.z, nL * 8, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(node.data(), L.node, nL * 4, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(dmask.data(), L.dmask, nL, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(owner.data(), L.owner, nL, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  // one sub-domain per SM, at least 8 elements each
+  const int B = std::max(1, std::min({nsm, L.E / 8, COARSE_GRID_MAX}));
+  PipeHost h;
+  SEM_TRY(pipe_partition(L.E, L.nG, node.data(), dmask.data(), owner.data(), xyz[0].data(), xyz[1].data(),
+                         xyz[2].data(), B, &h));
+  SEM_TRY(upload(&L.pp_el_off, h.el_off, s));
+  SEM_TRY(upload(&L.pp_el, h.el, s));
+  SEM_TRY(upload(&L.pp_p2n, h.p2n, s));
+  SEM_TRY(upload(&L.pp_nd_off, h.nd_off, s));
+  SEM_TRY(upload(&L.pp_nd_src, h.nd_src, s));
+  SEM_TRY(upload(&L.pp_nd_fl, h.nd_fl, s));
+  SEM_TRY(upload(&L.pp_cp_off, h.cp_off, s));
+  SEM_TRY(upload(&L.pp_cp, h.cp, s));
+  if (cudaMalloc((void**)&L.pp_xbuf, 2 * (size_t)nL * sizeof(double) + 16) != cudaSuccess ||
+      cudaMalloc((void**)&L.pp_part, 6 * (size_t)B * sizeof(double) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    set_detail("cudaMalloc failed (sub-domain coarse solve)");
+    return SEM_ENOMEM;
+  }
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  L.pp_max_el = h.max_el;
+  L.pp_max_nd = h.max_nd;
+  L.pp_max_cp = h.max_cp;
+  L.pp_blocks = B;
+  return SEM_OK;
+}
+
+namespace {
+
+template <typename T, typename GT, int NPT, bool SMEM_G>
+int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool* used) {
+  const size_t smem = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp).total;
+  if (smem > 220 * 1024) return SEM_OK;
+  const void* f = (const void*)k_coarse_pipe<T, GT, NPT, SMEM_G>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return SEM_OK;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, PT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return SEM_OK;
+  }
+  if (per_sm < 1 || L.pp_blocks > per_sm * nsm) return SEM_OK;
+  a.G = G;
+  Mat64 D = L.D;
+  void* args[] = {&a, &D};
+  SEM_CUDA_TRY(cudaMemsetAsync(a.flags, 0, (size_t)L.pp_blocks * sizeof(unsigned), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(a.err, 0, sizeof(int), s));
+  SEM_CUDA_TRY(cudaLaunchCooperativeKernel(f, dim3(L.pp_blocks), dim3(PT), args, smem, s));
+  *used = true;
+  return SEM_OK;
+}
+
+template <typename T, typename GT, int NPT>
+int launch_npt(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool* used) {
+  SEM_TRY((try_launch<T, GT, NPT, true>(L, G, a, nsm, s, used)));
+  if (*used) return SEM_OK;
+  return try_launch<T, GT, NPT, false>(L, G, a, nsm, s, used);
+}
+
+template <typename T, typename GT>
+int launch_pipe(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool* used) {
+  const int npt = (L.pp_max_nd + PT - 1) / PT;
+  if (npt <= 1) return launch_npt<T, GT, 1>(L, G, a, nsm, s, used);
+  if (npt <= 2) return launch_npt<T, GT, 2>(L, G, a, nsm, s, used);
+  if (npt <= 4) return launch_npt<T, GT, 4>(L, G, a, nsm, s, used);
+  return SEM_OK;   // larger sub-domains: the caller falls back
+}
+
+}  // namespace
+
+// Pipelined sub-domain coarse solve at order 1 (FP64, FP32 or BF16-factor V-cycles);
+// *used = false when it does not apply. bar: [COARSE_GRID_MAX] flags, err: [1].
+int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
+                      double tol, int maxit, double* sc, unsigned* bar, int* err, cudaStream_t s, bool* used) {
+  *used = false;
+  if (L.NP != NPC) return SEM_OK;
+  SEM_TRY(coarse_pipe_build(L, s));
+  if (L.pp_blocks < 1) return SEM_OK;
+  int dev = 0, nsm = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PipeArgs a{};
+  a.b = b;
+  a.x = x;
+  a.dinv = dinv;
+  a.xbuf = L.pp_xbuf;
+  a.nL = L.nL;
+  a.el_off = L.pp_el_off;
+  a.el = L.pp_el;
+  a.p2n = L.pp_p2n;
+  a.nd_off = L.pp_nd_off;
+  a.nd_src = L.pp_nd_src;
+  a.nd_fl = L.pp_nd_fl;
+  a.cp_off = L.pp_cp_off;
+  a.cp = L.pp_cp;
+  a.max_el = L.pp_max_el;
+  a.max_nd = L.pp_max_nd;
+  a.max_cp = L.pp_max_cp;
+  a.h1 = h1;
+  a.h2 = h2;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.part = L.pp_part;
+  a.flags = bar;
+  a.err = err;
+  a.sc = sc;
+  if (prec == SEM_FP64) return launch_pipe<double, double>(L, L.G, a, nsm, s, used);
+  if (prec == SEM_FP32) return launch_pipe<float, float>(L, L.G32, a, nsm, s, used);
+  return launch_pipe<float, __nv_bfloat16>(L, L.G16, a, nsm, s, used);
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" int sem_coarse_partition(int32_t E, int64_t nG, const int32_t* node, const uint8_t* dmask,
+                                    const uint8_t* owner, const double* x, const double* y, const double* z,
+                                    int32_t nblocks, int64_t cap_nodes, int64_t cap_copies, int32_t* el_off,
+                                    int32_t* el, int32_t* p2n, int32_t* nd_off, int32_t* nd_src, uint8_t* nd_fl,
+                                    int32_t* cp_off, int32_t* cp, int64_t* counts) {
+  if (!node || !dmask || !owner || !x || !y || !z || !el_off || !el || !p2n || !nd_off || !nd_src || !nd_fl ||
+      !cp_off || !cp || !counts) {
+    set_detail("sem_coarse_partition: NULL argument");
+    return SEM_EINVAL;
+  }
+  PipeHost h;
+  const int rc = pipe_partition(E, nG, node, dmask, owner, x, y, z, nblocks, &h);
+  if (rc != SEM_OK) return rc;
+  counts[0] = (int64_t)h.nd_src.size();
+  counts[1] = (int64_t)h.cp.size();
+  counts[2] = h.max_el;
+  counts[3] = h.max_nd;
+  counts[4] = h.max_cp;
+  if (counts[0] > cap_nodes || counts[1] > cap_copies) {
+    set_detail("sem_coarse_partition: %lld nodes and %lld copies exceed the capacities given",
+               (long long)counts[0], (long long)counts[1]);
+    return SEM_EINVAL;
+  }
+  std::copy(h.el_off.begin(), h.el_off.end(), el_off);
+  std::copy(h.el.begin(), h.el.end(), el);
+  std::copy(h.p2n.begin(), h.p2n.end(), p2n);
+  std::copy(h.nd_off.begin(), h.nd_off.end(), nd_off);
+  std::copy(h.nd_src.begin(), h.nd_src.end(), nd_src);
+  std::copy(h.nd_fl.begin(), h.nd_fl.end(), nd_fl);
+  std::copy(h.cp_off.begin(), h.cp_off.end(), cp_off);
+  std::copy(h.cp.begin(), h.cp.end(), cp);
+  return SEM_OK;
+}

@@ -115,6 +115,19 @@ struct Level {
   // on-chip cluster coarse solve: (CTA rank << 24 | offset) of every gather-scatter copy
   int32_t* cl_loc = nullptr;      // [n_seg_idx]
   int cl_loc_epc = 0;             // elements per CTA the locations were computed for
+  // sub-domain coarse solve (coarse_pipe.cu; built on first use at order 1)
+  int pp_blocks = 0;              // sub-domains, one block each; 0 not built, -1 does not apply
+  int pp_max_el = 0, pp_max_nd = 0, pp_max_cp = 0;   // largest sub-domain: elements, nodes, copy entries
+  int32_t* pp_el_off = nullptr;   // [B+1] offsets into pp_el
+  int32_t* pp_el = nullptr;       // [E] elements grouped by sub-domain, ascending within one
+  int32_t* pp_p2n = nullptr;      // [nL] per point in pp_el order: sub-domain node | bit 31 when published
+  int32_t* pp_nd_off = nullptr;   // [B+1] offsets into the node arrays
+  int32_t* pp_nd_src = nullptr;   // one local point of each sub-domain node (b and D^-1 are read there)
+  uint8_t* pp_nd_fl = nullptr;    // bit 0: the sub-domain holds the owner copy; bit 1: Dirichlet
+  int32_t* pp_cp_off = nullptr;   // [nodes + 1] offsets into pp_cp
+  int32_t* pp_cp = nullptr;       // copies in canonical order: >= 0 sub-domain point, < 0 -(local point + 1)
+  double* pp_xbuf = nullptr;      // [2][nL] exchange buffer (read as FP32 in FP32 solves)
+  double* pp_part = nullptr;      // [2][3][B] block partials
 };
 
 // Device scalar slots (double) used by the Krylov kernels.
@@ -206,6 +219,11 @@ constexpr int COARSE_GRID_MAX = 2048;   // largest grid; scratch: part[3 * COARS
 int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p, void* w, const void* dinv,
                       double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
                       cudaStream_t s, bool* used);
+
+// ---- coarse_pipe.cu: one-launch pipelined coarse Jacobi-PCG on sub-domains (cooperative launch)
+int coarse_pipe_build(Level& L, cudaStream_t s);
+int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
+                      double tol, int maxit, double* sc, unsigned* bar, int* err, cudaStream_t s, bool* used);
 
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);

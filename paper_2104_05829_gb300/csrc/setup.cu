@@ -223,7 +223,8 @@ void free_level(Level& L) {
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
-                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.cl_loc};
+                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.cl_loc, L.pp_el_off, L.pp_el,
+                  L.pp_p2n, L.pp_nd_off, L.pp_nd_src, L.pp_nd_fl, L.pp_cp_off, L.pp_cp, L.pp_xbuf, L.pp_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -412,7 +413,7 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   else sem_default_opts(&o);
   if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
       (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM) || o.coarse_mode < SEM_COARSE_AUTO ||
-      o.coarse_mode > SEM_COARSE_GRID) {
+      o.coarse_mode > SEM_COARSE_PIPE) {
     set_detail("invalid smoother / Lanczos / coarse-solve options");
     return SEM_EINVAL;
   }

@@ -235,11 +235,15 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   Level& L = C.lev[l];
   VecSet v = vecs(L, prec);
   double* sc = C.scal + 1 * S_NSLOTS;
-  // order 1: the whole solve in one cooperative launch over the whole GPU, or in
-  // one launch on one thread-block cluster with the problem on chip (FP32 /
-  // BF16-factor V-cycles)
+  // order 1: the whole solve in one cooperative launch over the whole GPU
+  // (pipelined on sub-domains, or per point), or in one launch on one
+  // thread-block cluster with the problem on chip (FP32 / BF16-factor V-cycles)
   bool used = false;
   const int mode = C.opts.coarse_mode;
+  if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_PIPE)
+    SEM_TRY(coarse_pipe_solve(L, prec, b, x, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol, C.opts.coarse_maxit, sc,
+                              C.cg_bar, C.cg_err, s, &used));
+  if (used) return SEM_OK;
   if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_GRID)
     SEM_TRY(coarse_grid_solve(L, prec, b, x, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
                               C.opts.coarse_maxit, sc, C.cg_part, C.cg_bar, C.cg_err, s, &used));
@@ -312,7 +316,11 @@ int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
   for (int l = 0; l < C.nlevels; ++l) {
     Level& L = C.lev[l];
     SEM_TRY(level_dinv(C, l, h1, h2, nullptr, L.dinv, L.dinv32, s));
-    if (l == C.nlevels - 1) continue;
+    if (l == C.nlevels - 1) {
+      if (C.opts.coarse_mode == SEM_COARSE_AUTO || C.opts.coarse_mode == SEM_COARSE_PIPE)
+        SEM_TRY(coarse_pipe_build(L, s));
+      continue;
+    }
     if (C.opts.smoother == SEM_SMOOTH_ASM) {
       SEM_TRY(schwarz_build(C, L, s));
       k_lanczos_start<<<vgrid(L.nL), 256, 0, s>>>(L.nL, L.label, L.dmask, C.opts.lanczos_seed, L.vb);

@@ -52,7 +52,8 @@ def default_opts(**kw) -> L.SemOpts:
             o.smoother = {"jacobi": L.SEM_SMOOTH_JACOBI, "asm": L.SEM_SMOOTH_ASM}.get(v, v)
         elif k == "coarse_mode":
             o.coarse_mode = {"auto": L.SEM_COARSE_AUTO, "cluster": L.SEM_COARSE_CLUSTER,
-                             "kernels": L.SEM_COARSE_KERNELS, "grid": L.SEM_COARSE_GRID}.get(v, v)
+                             "kernels": L.SEM_COARSE_KERNELS, "grid": L.SEM_COARSE_GRID,
+                             "pipe": L.SEM_COARSE_PIPE}.get(v, v)
         elif not hasattr(o, k):
             raise KeyError(k)
         else:
@@ -392,3 +393,30 @@ def gll(N: int):
     xi, rho, D = np.empty(N + 1), np.empty(N + 1), np.empty((N + 1, N + 1))
     L.check(lib.sem_gll(N, xi.ctypes.data, rho.ctypes.data, D.ctypes.data), "sem_gll")
     return xi, rho, D
+
+
+def coarse_partition(node, dmask, owner, x, y, z, n_G: int, nblocks: int) -> dict:
+    """The order-1 sub-domain partition of the pipelined coarse solve (host-side,
+    sem_coarse_partition); per-point inputs of length 8E, returns the arrays by name."""
+    lib = L.load()
+    node = np.ascontiguousarray(node, dtype=np.int32)
+    dmask = np.ascontiguousarray(dmask, dtype=np.uint8)
+    owner = np.ascontiguousarray(owner, dtype=np.uint8)
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (x, y, z))
+    nL = node.size
+    E = nL // 8
+    cap_n, cap_c = nL, 8 * nL
+    out = dict(el_off=np.empty(nblocks + 1, np.int32), el=np.empty(E, np.int32), p2n=np.empty(nL, np.int32),
+               nd_off=np.empty(nblocks + 1, np.int32), nd_src=np.empty(cap_n, np.int32),
+               nd_fl=np.empty(cap_n, np.uint8), cp_off=np.empty(cap_n + 1, np.int32), cp=np.empty(cap_c, np.int32))
+    counts = np.zeros(5, np.int64)
+    p = {k: v.ctypes.data for k, v in out.items()}
+    L.check(lib.sem_coarse_partition(E, int(n_G), node.ctypes.data, dmask.ctypes.data, owner.ctypes.data,
+                                      x.ctypes.data, y.ctypes.data, z.ctypes.data, nblocks, cap_n, cap_c,
+                                      p["el_off"], p["el"], p["p2n"], p["nd_off"], p["nd_src"], p["nd_fl"],
+                                      p["cp_off"], p["cp"], counts.ctypes.data), "sem_coarse_partition")
+    nn, nc = int(counts[0]), int(counts[1])
+    out["nd_src"], out["nd_fl"] = out["nd_src"][:nn], out["nd_fl"][:nn]
+    out["cp_off"], out["cp"] = out["cp_off"][:nn + 1], out["cp"][:nc]
+    out["max_el"], out["max_nd"], out["max_cp"] = (int(c) for c in counts[2:])
+    return out
