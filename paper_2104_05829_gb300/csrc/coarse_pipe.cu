@@ -21,12 +21,16 @@
 //   r = b, u = D^-1 r, w = A u (one extra synchronisation); for i = 0, 1, ...
 //     gamma = (r, u), delta = (w, u), rr = (r, r); m = D^-1 w; n = A m
 //     stop if rr <= tol^2 (b, b) or i = maxit (x is the result)
-//     beta = gamma / gamma_old (0 at i = 0), alpha = gamma / (delta - beta gamma / alpha_old)
+//     beta = gamma / gamma_old (0 at i = 0), pi = delta - beta^2 pi_old (= (p, A p)),
+//     alpha = gamma / pi
 //     z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
 //     x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
 // Dot products count each non-Dirichlet node once (in the block holding its
-// owner copy); block partials are summed in FP64, and every block adds all of
-// them in one fixed order, so all blocks take the same decisions.
+// owner copy); block partials (in the arithmetic type, published in FP64) are
+// added by every block in one fixed order, so all blocks take the same
+// decisions. The scalar step runs on one thread and keeps its FP64 work short
+// (GB300's FP64 pipe is narrow): 1 / gamma_old is formed earlier by another
+// thread, and the FP32 solve divides in FP32.
 // Synchronisation: a block publishes an epoch in its own flag after its writes;
 // the first warp of every block waits for all flags. The exchange buffer and the
 // partials are double-buffered by epoch parity: no block can be more than one
@@ -46,6 +50,7 @@ namespace sem {
 namespace {
 
 constexpr int PT = 512;             // threads per block
+constexpr int PIPE_MAX_BLOCKS = 256; // block partials are read eight per lane by one warp
 constexpr int PW = PT / 32;
 constexpr int NPC = 2;              // order 1
 constexpr int NPC3 = 8;
@@ -99,21 +104,64 @@ __device__ __forceinline__ double fval(double v) { return v; }
 __device__ __forceinline__ float fval(float v) { return v; }
 __device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // All blocks have written what they publish for this epoch once this returns.
-__device__ void sync_all(unsigned* flags, int* err, unsigned epoch) {
+// Release: the block barrier, then an acq_rel fence and the flag store by thread 0;
+// acquire: an acq_rel fence after the flags are seen, then the block barrier.
+// The first warp polls every block's flag, eight per lane per round trip. Waits
+// are bounded (about a second of SM clock); a wait that runs out, or that sees
+// another block's timeout, sets the global error flag and *s_err (shared), after
+// which this block waits no more.
+__device__ void sync_all(unsigned* flags, int* err, unsigned epoch, volatile int* s_err) {
   __syncthreads();
-  const bool live = *(volatile int*)err == 0;
-  if (threadIdx.x == 0 && live) {
-    __threadfence();
-    atomicExch(flags + blockIdx.x, epoch);
-  }
   if (threadIdx.x < 32) {
-    if (live)
-      for (unsigned q = threadIdx.x; q < gridDim.x; q += 32) wait_at_least(flags + q, epoch, err);
-    __threadfence();
+    if (threadIdx.x == 0) {
+      fence_acq_rel_gpu();
+      *(volatile unsigned*)(flags + blockIdx.x) = epoch;
+    }
+    __syncwarp();
+    if (*s_err == 0) {
+      const unsigned G = gridDim.x;
+      const long long t0 = clock64();
+      for (unsigned q0 = threadIdx.x; q0 < G; q0 += 32 * 8) {
+        unsigned polls = 0;
+        while (true) {
+          unsigned v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const unsigned q = q0 + 32 * k;
+            v[k] = q < G ? *(const volatile unsigned*)(flags + q) : epoch;
+          }
+          bool ok = true;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) ok = ok && v[k] >= epoch;
+          if (ok) break;
+          if ((++polls & 15u) == 0) {
+            if (*(volatile int*)err != 0) {
+              *s_err = 1;
+              break;
+            }
+            if (clock64() - t0 > (1ll << 31)) {
+              atomicExch(err, 1);
+              *s_err = 1;
+              break;
+            }
+          }
+        }
+      }
+    }
+    fence_acq_rel_gpu();
   }
   __syncthreads();
 }
+
+template <typename T>
+__device__ __forceinline__ T quotient(double n, double d);
+template <>
+__device__ __forceinline__ double quotient<double>(double n, double d) { return n / d; }
+template <>
+__device__ __forceinline__ float quotient<float>(double n, double d) { return (float)n / (float)d; }
 
 template <typename T, typename GT, int NPT, bool SMEM_G>
 __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
@@ -126,8 +174,11 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   int32_t* s_p2n = reinterpret_cast<int32_t*>(s_raw + lay.p2n);
   int32_t* s_cpo = reinterpret_cast<int32_t*>(s_raw + lay.cpo);
   int32_t* s_cp = reinterpret_cast<int32_t*>(s_raw + lay.cp);
-  __shared__ double s_red[PW][3];
+  __shared__ T s_red[PW][3];
+  __shared__ double s_tot[3];
+  __shared__ double s_gam, s_rgam;   // gamma of the last pass and its reciprocal
   __shared__ int s_flag;             // 0 go on, 1 converged, 2 breakdown, 3 iteration cap
+  __shared__ int s_err;              // a grid-wide wait ran out
   __shared__ T s_al, s_be;
   const int B = gridDim.x, bk = blockIdx.x;
   const int el0 = a.el_off[bk], nel = a.el_off[bk + 1] - el0, npt = nel * NPC3;
@@ -137,6 +188,10 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   const T* bv = static_cast<const T*>(a.b);
   const T* dv = static_cast<const T*>(a.dinv);
   T* xbuf = static_cast<T*>(a.xbuf);
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_gam = 1.0;
+  }
   for (int q = threadIdx.x; q < nel; q += PT) s_el[q] = a.el[el0 + q];
   for (int q = threadIdx.x; q < npt; q += PT) s_p2n[q] = a.p2n[(int64_t)el0 * NPC3 + q];
   for (int q = threadIdx.x; q <= nnd; q += PT) s_cpo[q] = a.cp_off[nd0 + q] - cp0;
@@ -246,13 +301,14 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
     if ((live >> c) & 1u) s_m[threadIdx.x + c * PT] = u[c];
   __syncthreads();
   apply(xbuf + (size_t)((epoch + 1) & 1u) * a.nL);
-  sync_all(a.flags, a.err, ++epoch);
+  sync_all(a.flags, a.err, ++epoch, &s_err);
 #pragma unroll
   for (int c = 0; c < NPT; ++c) w[c] = gather(c, xbuf + (size_t)(epoch & 1u) * a.nL);
 
   // scalar state, held by thread 0
-  double bb = 0, tol2 = 0, gam = 0, alpha_old = 0, rr = 0;
+  double bb = 0, tol2 = 0, den_old = 0, rr = 0;
   int flag = 0, it = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int pass = 0;; ++pass) {
     // gamma, delta, rr over owned nodes; m = D^-1 w
     T acc[3] = {T(0), T(0), T(0)};
@@ -266,63 +322,76 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
         acc[2] = fma(r[c], r[c], acc[2]);
       }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-      if (lane == 0) s_red[warp][t] = (double)acc[t];
+      if (lane == 0) s_red[warp][t] = acc[t];
     }
     __syncthreads();
     const unsigned par = (epoch + 1) & 1u;
-    if (threadIdx.x < 3) {
-      double t = 0;
-      for (int q = 0; q < PW; ++q) t += s_red[q][threadIdx.x];
-      __stcg(a.part + (size_t)par * 3 * B + (size_t)threadIdx.x * B + bk, t);
+    if (warp == 0) {
+      // block sums of the warp sums in a fixed tree, published in FP64
+      T v[3];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        v[t] = lane < PW ? s_red[lane][t] : T(0);
+#pragma unroll
+        for (int o = PW / 2; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
+      }
+      const T mine = lane == 0 ? v[0] : (lane == 1 ? v[1] : v[2]);
+      if (lane < 3) __stcg(a.part + (size_t)par * 3 * B + (size_t)lane * B + bk, (double)mine);
     }
     apply(xbuf + (size_t)par * a.nL);
-    sync_all(a.flags, a.err, ++epoch);
-    // n = QQ^T of the published outputs; the totals of the partials
+    sync_all(a.flags, a.err, ++epoch, &s_err);
+    // n = QQ^T of the published outputs; the last three warps add the block partials
+    // (their loads go out before the gathers), a fourth lane forms 1 / gamma_old
     const T* xb = xbuf + (size_t)(epoch & 1u) * a.nL;
+    const int tw = warp - (PW - 3);
+    double ld[8];
+    if (tw >= 0) {
+      const double* pp = a.part + (size_t)(epoch & 1u) * 3 * B + (size_t)tw * B;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) ld[kk] = lane + 32 * kk < B ? __ldcg(pp + lane + 32 * kk) : 0.0;
+    }
+    if (threadIdx.x == 32 * (PW - 4) && pass > 0) s_rgam = 1.0 / s_gam;
     T nv[NPT];
 #pragma unroll
     for (int c = 0; c < NPT; ++c) nv[c] = gather(c, xb);
-    if (threadIdx.x < 32) {
-      const double* pp = a.part + (size_t)(epoch & 1u) * 3 * B;
-      double tot[3];
+    if (tw >= 0) {
+      double v = ((ld[0] + ld[1]) + (ld[2] + ld[3])) + ((ld[4] + ld[5]) + (ld[6] + ld[7]));
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        double v = 0;
-        for (int q = threadIdx.x; q < B; q += 32) v += __ldcg(pp + (size_t)t * B + q);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        tot[t] = v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_tot[tw] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double gnew = s_tot[0], del = s_tot[1];
+      rr = s_tot[2];
+      if (pass == 0) {
+        bb = rr;
+        tol2 = a.tol * a.tol * bb;
       }
-      if (threadIdx.x == 0) {
-        const double gnew = tot[0], del = tot[1];
-        rr = tot[2];
-        if (pass == 0) {
-          bb = rr;
-          tol2 = a.tol * a.tol * bb;
-        }
-        it = pass;
-        int f = 0;
-        double alpha = 0, beta = 0;
-        if (*(volatile int*)a.err != 0 || !isfinite(rr)) f = 2;
-        else if (rr <= tol2) f = 1;
-        else if (pass >= a.maxit) f = 3;
-        else {
-          beta = pass == 0 ? 0.0 : gnew / gam;
-          const double den = pass == 0 ? del : del - beta * gnew / alpha_old;
-          alpha = gnew / den;
-          if (!(den > 0.0) || !(gnew > 0.0) || !isfinite(alpha)) f = 2;
-        }
-        gam = gnew;
-        alpha_old = alpha;
-        s_flag = f;
-        s_al = (T)alpha;
-        s_be = (T)beta;
+      it = pass;
+      int f = 0;
+      double beta = 0, den = 0;
+      T alpha = T(0);
+      if (s_err != 0 || !isfinite(rr)) f = 2;
+      else if (rr <= tol2) f = 1;
+      else if (pass >= a.maxit) f = 3;
+      else {
+        // (p, A p) = delta - beta^2 (p_old, A p_old), the pipelined form of
+        // delta - beta gamma / alpha_old
+        beta = pass == 0 ? 0.0 : gnew * s_rgam;
+        den = pass == 0 ? del : fma(-beta * beta, den_old, del);
+        alpha = quotient<T>(gnew, den);
+        if (!(den > 0.0) || !(gnew > 0.0) || !isfinite(alpha)) f = 2;
       }
+      den_old = den;
+      s_gam = gnew;
+      s_flag = f;
+      s_al = alpha;
+      s_be = (T)beta;
     }
     __syncthreads();
     flag = s_flag;
@@ -539,7 +608,7 @@ int coarse_pipe_build(Level& L, cudaStream_t s) {
   SEM_CUDA_TRY(cudaMemcpyAsync(owner.data(), L.owner, nL, cudaMemcpyDeviceToHost, s));
   SEM_CUDA_TRY(cudaStreamSynchronize(s));
   // one sub-domain per SM, at least 8 elements each
-  const int B = std::max(1, std::min({nsm, L.E / 8, COARSE_GRID_MAX}));
+  const int B = std::max(1, std::min({nsm, L.E / 8, PIPE_MAX_BLOCKS}));
   PipeHost h;
   SEM_TRY(pipe_partition(L.E, L.nG, node.data(), dmask.data(), owner.data(), xyz[0].data(), xyz[1].data(),
                          xyz[2].data(), B, &h));
@@ -617,7 +686,7 @@ int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* di
   *used = false;
   if (L.NP != NPC) return SEM_OK;
   SEM_TRY(coarse_pipe_build(L, s));
-  if (L.pp_blocks < 1) return SEM_OK;
+  if (L.pp_blocks < 1 || L.pp_blocks > PIPE_MAX_BLOCKS) return SEM_OK;
   int dev = 0, nsm = 0;
   SEM_CUDA_TRY(cudaGetDevice(&dev));
   SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

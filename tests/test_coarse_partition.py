@@ -151,7 +151,7 @@ def _emulate(L, p, b_g, dinv_g, h1, h2, maxit, tol):
     u = di * r
     w = apply(u)
     x, z, q, s, pv = (np.zeros(nn) for _ in range(5))
-    gam_old = alpha_old = bb = tol2 = 0.0
+    gam_old = pi_old = bb = tol2 = 0.0
     for it in range(maxit + 1):
         gam, dlt, rr = (float(np.sum((a * c)[own_n])) for a, c in ((r, u), (w, u), (r, r)))
         m = di * w
@@ -161,10 +161,11 @@ def _emulate(L, p, b_g, dinv_g, h1, h2, maxit, tol):
         if rr <= tol2 or it >= maxit:
             break
         beta = 0.0 if it == 0 else gam / gam_old
-        alpha = gam / (dlt if it == 0 else dlt - beta * gam / alpha_old)
+        pi = dlt if it == 0 else dlt - beta * beta * pi_old      # (p, A p)
+        alpha = gam / pi
         z, q, s, pv = n + beta * z, m + beta * q, w + beta * s, u + beta * pv
         x, r, u, w = x + alpha * pv, r - alpha * s, u - alpha * q, w - alpha * z
-        gam_old, alpha_old = gam, alpha
+        gam_old, pi_old = gam, pi
     return x, it, g_of
 
 
