@@ -31,10 +31,15 @@
 // decisions. The scalar step runs on one thread and keeps its FP64 work short
 // (GB300's FP64 pipe is narrow): 1 / gamma_old is formed earlier by another
 // thread, and the FP32 solve divides in FP32.
-// Synchronisation: a block publishes an epoch in its own flag after its writes;
-// the first warp of every block waits for all flags. The exchange buffer and the
-// partials are double-buffered by epoch parity: no block can be more than one
-// synchronisation ahead of another. Waits are bounded (about a second of SM
+// Exchange: the FP32 and BF16-factor solves publish each interface output and
+// each block partial as one 64-bit word holding the FP32 value and its epoch
+// (relaxed 64-bit accesses are single-copy atomic), and a block waits only on
+// the words it reads, with no fence and no grid barrier. The FP64 solve
+// publishes plain values, then a block publishes the epoch in its own flag
+// (release) and the first warp of every block waits for all flags (acquire).
+// Exchange buffer and partials are double-buffered by epoch parity: the dot
+// products couple every block once per iteration, so no block can overwrite a
+// word another block has still to read. Waits are bounded (about a second of SM
 // clock); after a timeout every wait ends at once and the solve reports a
 // breakdown.
 #include <algorithm>
@@ -163,8 +168,52 @@ __device__ __forceinline__ double quotient<double>(double n, double d) { return 
 template <>
 __device__ __forceinline__ float quotient<float>(double n, double d) { return (float)n / (float)d; }
 
+// Tagged words of the FP32 exchange: the value's bits low, its epoch high. Relaxed
+// 64-bit accesses at GPU scope are single-copy atomic, so a reader that sees the
+// epoch it waits for holds that epoch's value; no fence or flag is needed.
+__device__ __forceinline__ void st_tagged(uint64_t* p, float v, unsigned tag) {
+  const uint64_t w = ((uint64_t)tag << 32) | __float_as_uint(v);
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_tagged(const uint64_t* p) {
+  uint64_t w;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+__device__ __forceinline__ bool tag_is(uint64_t w, unsigned tag) { return (unsigned)(w >> 32) == tag; }
+__device__ __forceinline__ float tag_val(uint64_t w) { return __uint_as_float((unsigned)w); }
+
+// Bound of a wait on tagged words: go() is false once the wait has run about a
+// second of SM clock (then the global and block error flags are set) or another
+// block has given up.
+struct SpinBound {
+  long long t0;
+  unsigned polls;
+  __device__ SpinBound() {
+    t0 = clock64();
+    polls = 0;
+  }
+  __device__ bool go(int* err, volatile int* s_err) {
+    if ((++polls & 15u) != 0) return true;
+    if (*s_err != 0 || *(volatile int*)err != 0) {
+      *s_err = 1;
+      return false;
+    }
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicExch(err, 1);
+      *s_err = 1;
+      return false;
+    }
+    return true;
+  }
+};
+
+// FP32 and BF16-factor solves (T = float) exchange tagged words and wait only on
+// the words they read; the FP64 solve publishes plain values and synchronises the
+// grid with sync_all.
 template <typename T, typename GT, int NPT, bool SMEM_G>
 __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
+  constexpr bool TAG = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char s_raw[];
   const PipeSmem lay = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp);
   GT* sG = reinterpret_cast<GT*>(s_raw);
@@ -187,7 +236,9 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   const GT* G = static_cast<const GT*>(a.G);
   const T* bv = static_cast<const T*>(a.b);
   const T* dv = static_cast<const T*>(a.dinv);
-  T* xbuf = static_cast<T*>(a.xbuf);
+  T* xbuf = static_cast<T*>(a.xbuf);                        // [2][nL] values (FP64 solve)
+  uint64_t* xtag = static_cast<uint64_t*>(a.xbuf);          // [2][nL] tagged words (FP32 solves)
+  uint64_t* ptag = reinterpret_cast<uint64_t*>(a.part);     // [2][3][B] tagged partials (FP32 solves)
   if (threadIdx.x == 0) {
     s_err = 0;
     s_gam = 1.0;
@@ -211,6 +262,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   const T dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
   const T ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;
   const T h1 = (T)a.h1, h2 = (T)a.h2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // node state (slot c: node threadIdx.x + c * PT of the sub-domain)
   T x[NPT], r[NPT], u[NPT], w[NPT], z[NPT], qv[NPT], sv[NPT], p[NPT], di[NPT], mv[NPT];
   unsigned own = 0, dir = 0, live = 0;
@@ -234,49 +286,114 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   }
   __syncthreads();   // factors staged
 
-  // s_pt = A_L s_m on the sub-domain's points; interface points also go to xb
-  auto apply = [&](T* xb) {
+  // factors of chunk ch for this thread's point (global-memory factors are read
+  // one chunk ahead, so their L2 latency overlaps the previous chunk's work)
+  auto fetch_g = [&](int ch, T (&g)[7]) {
+    const int bp = threadIdx.x + ch * PT;
+    if (bp < npt) {
+      const GT* gp = SMEM_G ? sG + (bp >> 3) * GF + lq : G + (int64_t)s_el[bp >> 3] * GF + lq;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) g[k] = (T)fval(gp[8 * k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) g[k] = T(0);
+    }
+  };
+  // s_pt = A_L s_m on the sub-domain's points; interface points are also published
+  // for epoch ep
+  auto apply = [&](unsigned ep) {
     const int nch = (npt + PT - 1) / PT;
+    T gc[7], gn[7];
+    if (!SMEM_G) fetch_g(0, gc);
     for (int ch = 0; ch < nch; ++ch) {
       const int bp = threadIdx.x + ch * PT;
       const bool lv = bp < npt;
+      if (SMEM_G) fetch_g(ch, gc);
+      else if (ch + 1 < nch) fetch_g(ch + 1, gn);
       const int32_t pn = lv ? s_p2n[bp] : 0;
       const T uu = lv ? s_m[pn & NODE_MASK] : T(0);
       const T ur = di_s * uu + di_o * __shfl_xor_sync(0xffffffffu, uu, 1);
       const T us = dj_s * uu + dj_o * __shfl_xor_sync(0xffffffffu, uu, 2);
       const T ut = dk_s * uu + dk_o * __shfl_xor_sync(0xffffffffu, uu, 4);
-      T wr = T(0), ws = T(0), wt = T(0), bu = T(0);
-      if (lv) {
-        const GT* g = SMEM_G ? sG + (bp >> 3) * GF + lq : G + (int64_t)s_el[bp >> 3] * GF + lq;
-        const T g11 = (T)fval(g[0]), g12 = (T)fval(g[8]), g13 = (T)fval(g[16]);
-        const T g22 = (T)fval(g[24]), g23 = (T)fval(g[32]), g33 = (T)fval(g[40]);
-        wr = h1 * (g11 * ur + g12 * us + g13 * ut);
-        ws = h1 * (g12 * ur + g22 * us + g23 * ut);
-        wt = h1 * (g13 * ur + g23 * us + g33 * ut);
-        bu = h2 * (T)fval(g[48]) * uu;
-      }
+      // G11 G12 G13 G22 G23 G33 B (zero past the last point)
+      const T wr = h1 * (gc[0] * ur + gc[1] * us + gc[2] * ut);
+      const T ws = h1 * (gc[1] * ur + gc[3] * us + gc[4] * ut);
+      const T wt = h1 * (gc[2] * ur + gc[4] * us + gc[5] * ut);
+      const T bu = h2 * gc[6] * uu;
       T wv = bu + di_s * wr + ti_o * __shfl_xor_sync(0xffffffffu, wr, 1);
       wv += dj_s * ws + tj_o * __shfl_xor_sync(0xffffffffu, ws, 2);
       wv += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
       if (lv) {
         s_pt[bp] = wv;
-        if (pn < 0) __stcg(xb + (int64_t)s_el[bp >> 3] * NPC3 + lq, wv);
+        if (pn < 0) {
+          const size_t o = (size_t)(ep & 1u) * a.nL + (size_t)s_el[bp >> 3] * NPC3 + lq;
+          if constexpr (TAG) st_tagged(xtag + o, (float)wv, ep);
+          else __stcg(xbuf + o, wv);
+        }
+      }
+      if (!SMEM_G) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) gc[k] = gn[k];
       }
     }
   };
-  // assembled value of node slot c: every copy, in canonical order
-  auto gather = [&](int c, const T* xb) -> T {
+  // all blocks' outputs of epoch ep are published (FP64: grid barrier; FP32: the
+  // block's own outputs are in shared memory, the rest is awaited word by word)
+  auto exchange = [&](unsigned ep) {
+    if constexpr (TAG) __syncthreads();
+    else sync_all(a.flags, a.err, ep, &s_err);
+  };
+  // assembled value of node slot c at epoch ep: every copy, in canonical order
+  auto gather = [&](int c, unsigned ep) -> T {
     const int jn = threadIdx.x + c * PT;
     if (!((live >> c) & 1u) || ((dir >> c) & 1u)) return T(0);
     const int q0 = s_cpo[jn], m = s_cpo[jn + 1] - q0;
+    const size_t base = (size_t)(ep & 1u) * a.nL;
+    T v[8];
     if (m <= 8) {
-      T v[8];
+      if constexpr (TAG) {
+        int32_t lr[8];
+        uint64_t wd[8];
+        unsigned need = 0;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        v[t] = T(0);
-        if (t < m) {
-          const int32_t e = s_cp[q0 + t];
-          v[t] = e >= 0 ? s_pt[e] : __ldcg(xb + (-(int64_t)e - 1));
+        for (int t = 0; t < 8; ++t) {
+          v[t] = T(0);
+          lr[t] = 0;
+          wd[t] = 0;
+          if (t < m) {
+            const int32_t e = s_cp[q0 + t];
+            if (e >= 0) {
+              v[t] = s_pt[e];
+            } else {
+              lr[t] = -e - 1;
+              need |= 1u << t;
+            }
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if ((need >> t) & 1u) wd[t] = ld_tagged(xtag + base + lr[t]);
+        SpinBound sb;
+        while (true) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (((need >> t) & 1u) && tag_is(wd[t], ep)) {
+              v[t] = tag_val(wd[t]);
+              need &= ~(1u << t);
+            }
+          if (need == 0 || !sb.go(a.err, &s_err)) break;
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if ((need >> t) & 1u) wd[t] = ld_tagged(xtag + base + lr[t]);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          v[t] = T(0);
+          if (t < m) {
+            const int32_t e = s_cp[q0 + t];
+            v[t] = e >= 0 ? s_pt[e] : __ldcg(xbuf + base + (-(int64_t)e - 1));
+          }
         }
       }
       T sum = v[0];
@@ -288,8 +405,19 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
     T sum = T(0);
     for (int t = 0; t < m; ++t) {
       const int32_t e = s_cp[q0 + t];
-      const T v = e >= 0 ? s_pt[e] : __ldcg(xb + (-(int64_t)e - 1));
-      sum = t == 0 ? v : sum + v;
+      T vt;
+      if (e >= 0) {
+        vt = s_pt[e];
+      } else if constexpr (TAG) {
+        const uint64_t* wp = xtag + base + (-(int64_t)e - 1);
+        uint64_t wd = ld_tagged(wp);
+        SpinBound sb;
+        while (!tag_is(wd, ep) && sb.go(a.err, &s_err)) wd = ld_tagged(wp);
+        vt = tag_val(wd);
+      } else {
+        vt = __ldcg(xbuf + base + (-(int64_t)e - 1));
+      }
+      sum = t == 0 ? vt : sum + vt;
     }
     return sum;
   };
@@ -300,16 +428,17 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   for (int c = 0; c < NPT; ++c)
     if ((live >> c) & 1u) s_m[threadIdx.x + c * PT] = u[c];
   __syncthreads();
-  apply(xbuf + (size_t)((epoch + 1) & 1u) * a.nL);
-  sync_all(a.flags, a.err, ++epoch, &s_err);
+  ++epoch;
+  apply(epoch);
+  exchange(epoch);
 #pragma unroll
-  for (int c = 0; c < NPT; ++c) w[c] = gather(c, xbuf + (size_t)(epoch & 1u) * a.nL);
+  for (int c = 0; c < NPT; ++c) w[c] = gather(c, epoch);
 
   // scalar state, held by thread 0
   double bb = 0, tol2 = 0, den_old = 0, rr = 0;
   int flag = 0, it = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int pass = 0;; ++pass) {
+    ++epoch;
     // gamma, delta, rr over owned nodes; m = D^-1 w
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -329,9 +458,9 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
       if (lane == 0) s_red[warp][t] = acc[t];
     }
     __syncthreads();
-    const unsigned par = (epoch + 1) & 1u;
+    const size_t pbase = (size_t)(epoch & 1u) * 3 * B;
     if (warp == 0) {
-      // block sums of the warp sums in a fixed tree, published in FP64
+      // block sums of the warp sums in a fixed tree
       T v[3];
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
@@ -340,25 +469,55 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
         for (int o = PW / 2; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
       }
       const T mine = lane == 0 ? v[0] : (lane == 1 ? v[1] : v[2]);
-      if (lane < 3) __stcg(a.part + (size_t)par * 3 * B + (size_t)lane * B + bk, (double)mine);
+      if (lane < 3) {
+        if constexpr (TAG) st_tagged(ptag + pbase + (size_t)lane * B + bk, (float)mine, epoch);
+        else __stcg(a.part + pbase + (size_t)lane * B + bk, (double)mine);
+      }
     }
-    apply(xbuf + (size_t)par * a.nL);
-    sync_all(a.flags, a.err, ++epoch, &s_err);
+    apply(epoch);
+    exchange(epoch);
     // n = QQ^T of the published outputs; the last three warps add the block partials
     // (their loads go out before the gathers), a fourth lane forms 1 / gamma_old
-    const T* xb = xbuf + (size_t)(epoch & 1u) * a.nL;
     const int tw = warp - (PW - 3);
     double ld[8];
+    uint64_t wd[8];
+    unsigned need = 0;
     if (tw >= 0) {
-      const double* pp = a.part + (size_t)(epoch & 1u) * 3 * B + (size_t)tw * B;
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) ld[kk] = lane + 32 * kk < B ? __ldcg(pp + lane + 32 * kk) : 0.0;
+      for (int kk = 0; kk < 8; ++kk) {
+        const int q = lane + 32 * kk;
+        ld[kk] = 0.0;
+        wd[kk] = 0;
+        if (q < B) {
+          if constexpr (TAG) {
+            wd[kk] = ld_tagged(ptag + pbase + (size_t)tw * B + q);
+            need |= 1u << kk;
+          } else {
+            ld[kk] = __ldcg(a.part + pbase + (size_t)tw * B + q);
+          }
+        }
+      }
     }
     if (threadIdx.x == 32 * (PW - 4) && pass > 0) s_rgam = 1.0 / s_gam;
     T nv[NPT];
 #pragma unroll
-    for (int c = 0; c < NPT; ++c) nv[c] = gather(c, xb);
+    for (int c = 0; c < NPT; ++c) nv[c] = gather(c, epoch);
     if (tw >= 0) {
+      if constexpr (TAG) {
+        SpinBound sb;
+        while (true) {
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            if (((need >> kk) & 1u) && tag_is(wd[kk], epoch)) {
+              ld[kk] = (double)tag_val(wd[kk]);
+              need &= ~(1u << kk);
+            }
+          if (need == 0 || !sb.go(a.err, &s_err)) break;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            if ((need >> kk) & 1u) wd[kk] = ld_tagged(ptag + pbase + (size_t)tw * B + lane + 32 * kk);
+        }
+      }
       double v = ((ld[0] + ld[1]) + (ld[2] + ld[3])) + ((ld[4] + ld[5]) + (ld[6] + ld[7]));
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -656,6 +815,10 @@ int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool
   void* args[] = {&a, &D};
   SEM_CUDA_TRY(cudaMemsetAsync(a.flags, 0, (size_t)L.pp_blocks * sizeof(unsigned), s));
   SEM_CUDA_TRY(cudaMemsetAsync(a.err, 0, sizeof(int), s));
+  if (sizeof(T) == 4) {   // tagged exchange: epochs start at 1, so no stale word matches
+    SEM_CUDA_TRY(cudaMemsetAsync(a.xbuf, 0, 2 * (size_t)L.nL * sizeof(uint64_t), s));
+    SEM_CUDA_TRY(cudaMemsetAsync(a.part, 0, 6 * (size_t)L.pp_blocks * sizeof(uint64_t), s));
+  }
   SEM_CUDA_TRY(cudaLaunchCooperativeKernel(f, dim3(L.pp_blocks), dim3(PT), args, smem, s));
   *used = true;
   return SEM_OK;

@@ -126,8 +126,8 @@ struct Level {
   uint8_t* pp_nd_fl = nullptr;    // bit 0: the sub-domain holds the owner copy; bit 1: Dirichlet
   int32_t* pp_cp_off = nullptr;   // [nodes + 1] offsets into pp_cp
   int32_t* pp_cp = nullptr;       // copies in canonical order: >= 0 sub-domain point, < 0 -(local point + 1)
-  double* pp_xbuf = nullptr;      // [2][nL] exchange buffer (read as FP32 in FP32 solves)
-  double* pp_part = nullptr;      // [2][3][B] block partials
+  double* pp_xbuf = nullptr;      // [2][nL] exchange buffer (FP64 values, or tagged FP32 words)
+  double* pp_part = nullptr;      // [2][3][B] block partials (FP64, or tagged FP32 words)
 };
 
 // Device scalar slots (double) used by the Krylov kernels.

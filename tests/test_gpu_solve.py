@@ -250,6 +250,24 @@ def test_coarse_solve_executions_agree(prec, tol):
         assert relmax(zs[mode], zs["kernels"]) < tol, mode
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pipelined_coarse_solve_is_deterministic(prec):
+    """Every block of the pipelined coarse solve adds the same copies and the same block
+    partials in the same order, so repeated V-cycles (each a fresh cooperative launch whose
+    blocks run in a different interleaving) return identical bits; a torn or stale read of
+    the exchanged words would show up as a difference."""
+    dev()
+    mesh = si.box_mesh((6, 5, 4), 7, warp=0.1, perm_seed=2, dirichlet=("x0",))
+    L0 = O.level_from_mesh(mesh)
+    r = T(_gL(L0, L0.mask(np.random.default_rng(11).standard_normal(L0.n_G))))
+    ctx = ctx_for(mesh, mg_orders=[7, 3, 1], coarse_tol=1e-6, coarse_maxit=200, coarse_mode="pipe")
+    ctx.precond_setup(1.0, 0.0, prec)
+    z0 = H(ctx.vcycle(r))
+    for _ in range(5):
+        assert np.array_equal(H(ctx.vcycle(r)), z0)
+    ctx.close()
+
+
 def test_coarse_grid_solve_on_the_48cube_coarse_level():
     """At 48^3 elements the coarse level (110,592 order-1 elements) needs 32 points per
     thread with the factors read from global memory in the per-point cooperative solve, and
