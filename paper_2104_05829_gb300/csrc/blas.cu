@@ -25,10 +25,16 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
     k_dot(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const uint8_t* __restrict__ own,
           double* part, unsigned* ticket, double* out) {
+  struct V {
+    T a, b;
+    uint8_t o;
+  };
   Sums<1> acc{{0}};
-  GRID_LOOP(l, n) {
-    if (own[l]) acc.v[0] = fma((double)a[l], (double)b[l], acc.v[0]);
-  }
+  grid_loop_u<4>(
+      n, [&](int64_t l) { return V{a[l], b[l], own[l]}; },
+      [&](int64_t, const V& v) {
+        if (v.o) acc.v[0] = fma((double)v.a, (double)v.b, acc.v[0]);
+      });
   reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) { *out = t.v[0]; });
 }
 
@@ -73,10 +79,16 @@ __global__ void __launch_bounds__(RED_THREADS)
     k_alpha(int64_t n, const T* __restrict__ p, const T* __restrict__ w, const uint8_t* __restrict__ own,
             double* part, unsigned* ticket, double* sc) {
   if (skip(sc)) return;
+  struct V {
+    T p, w;
+    uint8_t o;
+  };
   Sums<1> acc{{0}};
-  GRID_LOOP(l, n) {
-    if (own[l]) acc.v[0] = fma((double)p[l], (double)w[l], acc.v[0]);
-  }
+  grid_loop_u<4>(
+      n, [&](int64_t l) { return V{p[l], w[l], own[l]}; },
+      [&](int64_t, const V& v) {
+        if (v.o) acc.v[0] = fma((double)v.p, (double)v.w, acc.v[0]);
+      });
   reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) {
     const double pw = t.v[0];
     sc[S_PW] = pw;
@@ -98,17 +110,23 @@ __global__ void __launch_bounds__(RED_THREADS)
                     double* part, unsigned* ticket, double* sc) {
   if (skip(sc)) return;
   const T a = (T)sc[S_ALPHA];
+  struct V {
+    T x, p, r, w, d;
+    uint8_t o;
+  };
   Sums<2> acc{{0, 0}};
-  GRID_LOOP(l, n) {
-    x[l] = fma(a, p[l], x[l]);
-    const T rl = fma(-a, w[l], r[l]);
-    r[l] = rl;
-    if (own[l]) {
-      const double rd = (double)rl;
-      acc.v[0] = fma(rd, rd, acc.v[0]);
-      acc.v[1] = fma(rd, (double)(dinv[l] * rl), acc.v[1]);
-    }
-  }
+  grid_loop_u<4>(
+      n, [&](int64_t l) { return V{x[l], p[l], r[l], w[l], dinv[l], own[l]}; },
+      [&](int64_t l, const V& v) {
+        x[l] = fma(a, v.p, v.x);
+        const T rl = fma(-a, v.w, v.r);
+        r[l] = rl;
+        if (v.o) {
+          const double rd = (double)rl;
+          acc.v[0] = fma(rd, rd, acc.v[0]);
+          acc.v[1] = fma(rd, (double)(v.d * rl), acc.v[1]);
+        }
+      });
   reduce_finish<2>(acc, part, ticket, [=] __device__(const Sums<2>& t) {
     sc[S_RR] = t.v[0];
     sc[S_ITER] += 1;
@@ -138,15 +156,20 @@ __global__ void __launch_bounds__(RED_THREADS)
                   double* part, unsigned* ticket, double* sc) {
   if (skip(sc)) return;
   const double a = sc[S_ALPHA];
+  struct V {
+    double x, p, r, w;
+    uint8_t o;
+  };
   Sums<1> acc{{0}};
-  GRID_LOOP(l, n) {
-    x[l] = fma(a, p[l], x[l]);
-    const double ro = r[l];
-    const double rn = fma(-a, w[l], ro);
-    r[l] = rn;
-    dr[l] = rn - ro;
-    if (own[l]) acc.v[0] = fma(rn, rn, acc.v[0]);
-  }
+  grid_loop_u<4>(
+      n, [&](int64_t l) { return V{x[l], p[l], r[l], w[l], own[l]}; },
+      [&](int64_t l, const V& v) {
+        x[l] = fma(a, v.p, v.x);
+        const double rn = fma(-a, v.w, v.r);
+        r[l] = rn;
+        dr[l] = rn - v.r;
+        if (v.o) acc.v[0] = fma(rn, rn, acc.v[0]);
+      });
   reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) {
     sc[S_RR] = t.v[0];
     sc[S_ITER] += 1;
@@ -162,14 +185,19 @@ __global__ void __launch_bounds__(RED_THREADS)
     k_beta_flex(int64_t n, const double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ dr,
                 const uint8_t* __restrict__ own, double* part, unsigned* ticket, double* sc) {
   if (skip(sc)) return;
+  struct V {
+    double z, r, d;
+    uint8_t o;
+  };
   Sums<2> acc{{0, 0}};
-  GRID_LOOP(l, n) {
-    if (own[l]) {
-      const double zl = z[l];
-      acc.v[0] = fma(zl, r[l], acc.v[0]);
-      acc.v[1] = fma(zl, dr[l], acc.v[1]);
-    }
-  }
+  grid_loop_u<4>(
+      n, [&](int64_t l) { return V{z[l], r[l], dr[l], own[l]}; },
+      [&](int64_t, const V& v) {
+        if (v.o) {
+          acc.v[0] = fma(v.z, v.r, acc.v[0]);
+          acc.v[1] = fma(v.z, v.d, acc.v[1]);
+        }
+      });
   reduce_finish<2>(acc, part, ticket, [=] __device__(const Sums<2>& t) {
     sc[S_BETA] = t.v[1] / sc[S_RZ];
     sc[S_RZ] = t.v[0];

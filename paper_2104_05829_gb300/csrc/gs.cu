@@ -5,7 +5,9 @@
 // local copy and Dirichlet nodes. Interior (singleton) points are never touched.
 // One thread per segment sums its copies in ascending local-index order (a
 // fixed order, so results are reproducible) and writes the sum back to every
-// copy; a Dirichlet segment writes zeros when the mask is requested.
+// copy; a Dirichlet segment writes zeros when the mask is requested. Segments of
+// up to eight copies (every node of a conforming hexahedral mesh) issue all their
+// index and value loads before the first add.
 #include "sem_internal.cuh"
 
 namespace sem {
@@ -18,12 +20,28 @@ __global__ void k_gs(int64_t nseg, const int32_t* __restrict__ off, const int32_
   if (skip && *skip != 0.0) return;
   const int64_t sgi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (sgi >= nseg) return;
-  const int b = off[sgi], e = off[sgi + 1];
+  const int b = off[sgi], e = off[sgi + 1], m = e - b;
   if (mask && sdir[sgi]) {
     for (int p = b; p < e; ++p) w[idx[p]] = T(0);
     return;
   }
-  if (e - b < 2) return;
+  if (m < 2) return;
+  if (m <= 8) {
+    int id[8];
+    T v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) id[t] = t < m ? idx[b + t] : 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = t < m ? w[id[t]] : T(0);
+    T s = v[0];
+#pragma unroll
+    for (int t = 1; t < 8; ++t)
+      if (t < m) s += v[t];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t < m) w[id[t]] = s;
+    return;
+  }
   T s = w[idx[b]];
   for (int p = b + 1; p < e; ++p) s += w[idx[p]];
   for (int p = b; p < e; ++p) w[idx[p]] = s;

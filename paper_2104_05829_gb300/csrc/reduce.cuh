@@ -79,4 +79,24 @@ __device__ void reduce_finish(Sums<NS> a, double* part, unsigned* ticket, Fin fi
 #define GRID_LOOP(l, n) \
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < (n); l += (int64_t)gridDim.x * blockDim.x)
 
+// Grid-stride loop that takes U points a grid stride apart per trip: ld(l) for all
+// U points first, then op(l, loaded) for each in order, so a thread keeps U points'
+// loads in flight while earlier arithmetic (on GB300 often the narrow FP64 pipe)
+// runs. The tail takes one point per trip. Each thread visits its points in a
+// fixed order, so sums stay deterministic.
+template <int U, class Ld, class Op>
+__device__ __forceinline__ void grid_loop_u(int64_t n, Ld ld, Op op) {
+  using V = decltype(ld(int64_t(0)));
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; l + (U - 1) * S < n; l += U * S) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld(l + u * S);
+#pragma unroll
+    for (int u = 0; u < U; ++u) op(l + u * S, v[u]);
+  }
+  for (; l < n; l += S) op(l, ld(l));
+}
+
 }  // namespace sem
