@@ -150,10 +150,13 @@ __global__ void k_direction_jacobi(int64_t n, T* __restrict__ p, const T* __rest
 }
 
 // ---- flexible CG (FP64) ----------------------------------------------------------
+// x += a p, r -= a w, (r, r); rb (may be null) receives r in the V-cycle's type, so
+// the preconditioner reads its input without a conversion pass.
+template <typename RB>
 __global__ void __launch_bounds__(RED_THREADS)
     k_update_flex(int64_t n, double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
-                  const double* __restrict__ w, double* __restrict__ dr, const uint8_t* __restrict__ own,
-                  double* part, unsigned* ticket, double* sc) {
+                  const double* __restrict__ w, RB* __restrict__ rb, const uint8_t* __restrict__ own, double* part,
+                  unsigned* ticket, double* sc) {
   if (skip(sc)) return;
   const double a = sc[S_ALPHA];
   struct V {
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(RED_THREADS)
         x[l] = fma(a, v.p, v.x);
         const double rn = fma(-a, v.w, v.r);
         r[l] = rn;
-        dr[l] = rn - v.r;
+        if (rb) rb[l] = (RB)rn;
         if (v.o) acc.v[0] = fma(rn, rn, acc.v[0]);
       });
   reduce_finish<1>(acc, part, ticket, [=] __device__(const Sums<1>& t) {
@@ -181,38 +184,46 @@ __global__ void __launch_bounds__(RED_THREADS)
   });
 }
 
+// Flexible (Polak-Ribiere) beta = (z, r_new - r_old) / (z_old, r_old). With
+// r_new = r_old - alpha w the numerator is -alpha (z, w), so the kernel reads w
+// (still held from the operator) instead of a stored difference; w = null (the
+// first direction) gives beta = 0. z is the V-cycle's output in its own type.
+template <typename ZT>
 __global__ void __launch_bounds__(RED_THREADS)
-    k_beta_flex(int64_t n, const double* __restrict__ z, const double* __restrict__ r, const double* __restrict__ dr,
+    k_beta_flex(int64_t n, const ZT* __restrict__ z, const double* __restrict__ r, const double* __restrict__ w,
                 const uint8_t* __restrict__ own, double* part, unsigned* ticket, double* sc) {
   if (skip(sc)) return;
   struct V {
-    double z, r, d;
+    double z, r, w;
     uint8_t o;
   };
   Sums<2> acc{{0, 0}};
   grid_loop_u<4>(
-      n, [&](int64_t l) { return V{z[l], r[l], dr[l], own[l]}; },
+      n, [&](int64_t l) { return V{(double)z[l], r[l], w ? w[l] : 0.0, own[l]}; },
       [&](int64_t, const V& v) {
         if (v.o) {
           acc.v[0] = fma(v.z, v.r, acc.v[0]);
-          acc.v[1] = fma(v.z, v.d, acc.v[1]);
+          acc.v[1] = fma(v.z, v.w, acc.v[1]);
         }
       });
+  const bool first = w == nullptr;
   reduce_finish<2>(acc, part, ticket, [=] __device__(const Sums<2>& t) {
-    sc[S_BETA] = t.v[1] / sc[S_RZ];
+    const double zdr = first ? 0.0 : -sc[S_ALPHA] * t.v[1];
+    sc[S_BETA] = zdr / sc[S_RZ];
     sc[S_RZ] = t.v[0];
-    sc[S_ZDR] = t.v[1];
-    if (!isfinite(t.v[0]) || !isfinite(t.v[1])) {
+    sc[S_ZDR] = zdr;
+    if (!isfinite(t.v[0]) || !isfinite(zdr)) {
       sc[S_BREAK] = 1;
       sc[S_DONE] = 1;
     }
   });
 }
 
-__global__ void k_direction(int64_t n, double* __restrict__ p, const double* __restrict__ z, const double* sc) {
+template <typename ZT>
+__global__ void k_direction(int64_t n, double* __restrict__ p, const ZT* __restrict__ z, const double* sc) {
   if (skip(sc)) return;
   const double beta = sc[S_BETA];
-  GRID_LOOP(l, n) p[l] = fma(beta, p[l], z[l]);
+  GRID_LOOP(l, n) p[l] = fma(beta, p[l], (double)z[l]);
 }
 
 // ---- Chebyshev-Jacobi pieces (no reductions) -------------------------------------
@@ -382,22 +393,33 @@ int kr_direction_jacobi(const Level& L, int prec, void* p, const void* r, const 
   return SEM_OK;
 }
 
-int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, double* dr,
-                   double* sc, cudaStream_t s) {
-  k_update_flex<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, x, p, r, w, dr, L.owner, C.red_part, C.red_ticket, sc);
+int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, void* rb,
+                   int rb_prec, double* sc, cudaStream_t s) {
+  if (rb_prec == SEM_FP64)
+    k_update_flex<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, x, p, r, w, (double*)rb, L.owner, C.red_part,
+                                                             C.red_ticket, sc);
+  else
+    k_update_flex<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, x, p, r, w, (float*)rb, L.owner, C.red_part,
+                                                            C.red_ticket, sc);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
 
-int kr_beta_flex(Ctx& C, const Level& L, const double* z, const double* r, const double* dr, double* sc,
+int kr_beta_flex(Ctx& C, const Level& L, const void* z, int z_prec, const double* r, const double* w, double* sc,
                  cudaStream_t s) {
-  k_beta_flex<<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, z, r, dr, L.owner, C.red_part, C.red_ticket, sc);
+  if (z_prec == SEM_FP64)
+    k_beta_flex<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const double*)z, r, w, L.owner, C.red_part,
+                                                           C.red_ticket, sc);
+  else
+    k_beta_flex<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(L.nL, (const float*)z, r, w, L.owner, C.red_part,
+                                                          C.red_ticket, sc);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
 
-int kr_direction(const Level& L, double* p, const double* z, double* sc, cudaStream_t s) {
-  k_direction<<<vgrid(L.nL), 256, 0, s>>>(L.nL, p, z, sc);
+int kr_direction(const Level& L, double* p, const void* z, int z_prec, double* sc, cudaStream_t s) {
+  if (z_prec == SEM_FP64) k_direction<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, p, (const double*)z, sc);
+  else k_direction<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, p, (const float*)z, sc);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }

@@ -176,7 +176,7 @@ struct Ctx {
   double* scal = nullptr;           // [4 * S_NSLOTS]: outer, coarse, spare
   double* h_scal = nullptr;         // pinned mirror
   // fine-level FP64 solver workspace
-  double *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *dr = nullptr, *t = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *t = nullptr;
   // preconditioner
   bool pc_ready = false;
   int pc_prec = SEM_FP64;
@@ -250,11 +250,13 @@ int kr_update_jacobi(Ctx& C, const Level& L, int prec, void* x, const void* p, v
                      const void* dinv, double* sc, cudaStream_t s);
 int kr_direction_jacobi(const Level& L, int prec, void* p, const void* r, const void* dinv, double* sc,
                         cudaStream_t s);
-int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, double* dr,
-                   double* sc, cudaStream_t s);
-int kr_beta_flex(Ctx& C, const Level& L, const double* z, const double* r, const double* dr, double* sc,
+// flexible CG: rb (may be null) receives r in the V-cycle's type rb_prec; z is the
+// V-cycle's output in type z_prec; w = null in kr_beta_flex gives beta = 0
+int kr_update_flex(Ctx& C, const Level& L, double* x, const double* p, double* r, const double* w, void* rb,
+                   int rb_prec, double* sc, cudaStream_t s);
+int kr_beta_flex(Ctx& C, const Level& L, const void* z, int z_prec, const double* r, const double* w, double* sc,
                  cudaStream_t s);
-int kr_direction(const Level& L, double* p, const double* z, double* sc, cudaStream_t s);
+int kr_direction(const Level& L, double* p, const void* z, int z_prec, double* sc, cudaStream_t s);
 int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, void* d, bool x_zero,
                double inv_theta, cudaStream_t s);
 int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, void* d, double c1, double c2,

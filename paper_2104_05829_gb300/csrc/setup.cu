@@ -373,7 +373,7 @@ void sem_free(sem_ctx* h) {
   if (!C) return;
   for (int l = 0; l < SEM_MAX_LEVELS; ++l) free_level(C->lev[l]);
   advect_free(C->adv);
-  void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->dr, C->t,
+  void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->t,
                   C->cg_part, C->cg_bar, C->cg_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -499,7 +499,6 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   STEP(dmalloc(&C->z, nL));
   STEP(dmalloc(&C->p, nL));
   STEP(dmalloc(&C->w, nL));
-  STEP(dmalloc(&C->dr, nL));
   STEP(dmalloc(&C->t, nL));
   CUSTEP(cudaEventCreateWithFlags(&C->ev, cudaEventDisableTiming));
   CUSTEP(cudaEventCreateWithFlags(&C->cev[0], cudaEventDisableTiming));

@@ -699,18 +699,22 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
       SEM_TRY(precond_setup(*C, c->h1, c->h2, prec, s));
     SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, nullptr, nullptr, sc, tol, s, bbref));
     SEM_CUDA_TRY(cudaMemsetAsync(C->p, 0, n * 8, s));
-    SEM_CUDA_TRY(cudaMemsetAsync(C->dr, 0, n * 8, s));
     SEM_TRY(read_scalars(*C, 0, s));
     bb = C->h_scal[S_BB];
     rr = C->h_scal[S_RR];
     if (C->h_scal[S_DONE] == 0.0) {
-      SEM_TRY(vcycle(*C, prec, C->r, C->z, s));
-      SEM_TRY(kr_beta_flex(*C, L, C->z, C->r, C->dr, sc, s));
-      SEM_TRY(kr_direction(L, C->p, C->z, sc, s));
+      // the V-cycle reads r from the finest level's b and leaves z in its x, both
+      // in the V-cycle's type: the update kernel writes b, beta and the direction read x
+      const VecSet v0 = vecs(C->lev[0], prec);
+      const int vp = prec == SEM_FP64 ? SEM_FP64 : SEM_FP32;
+      SEM_TRY(vec_copy_convert(C->r, SEM_FP64, v0.b, vp, n, s));
+      SEM_TRY(vcycle_level(*C, 0, prec, s));
+      SEM_TRY(kr_beta_flex(*C, L, v0.x, vp, C->r, nullptr, sc, s));
+      SEM_TRY(kr_direction(L, C->p, v0.x, vp, sc, s));
       for (int k = 0; k < maxit; ++k) {
         SEM_TRY(outer_ax(C->p, w, nullptr, s));
         SEM_TRY(kr_alpha(*C, L, SEM_FP64, C->p, w, sc, s));
-        SEM_TRY(kr_update_flex(*C, L, u, C->p, C->r, w, C->dr, sc, s));
+        SEM_TRY(kr_update_flex(*C, L, u, C->p, C->r, w, v0.b, vp, sc, s));
         SEM_TRY(read_scalars(*C, 0, s));
         const double* hs = C->h_scal;
         rr = hs[S_RR];
@@ -720,9 +724,9 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
           break;
         }
         if (hs[S_DONE] != 0.0) break;
-        SEM_TRY(vcycle(*C, prec, C->r, C->z, s));
-        SEM_TRY(kr_beta_flex(*C, L, C->z, C->r, C->dr, sc, s));
-        SEM_TRY(kr_direction(L, C->p, C->z, sc, s));
+        SEM_TRY(vcycle_level(*C, 0, prec, s));
+        SEM_TRY(kr_beta_flex(*C, L, v0.x, vp, C->r, w, sc, s));
+        SEM_TRY(kr_direction(L, C->p, v0.x, vp, sc, s));
       }
       if (rc == SEM_OK && C->h_scal[S_DONE] == 0.0) rc = SEM_ENOTCONV;
     }
