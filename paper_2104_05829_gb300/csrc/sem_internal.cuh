@@ -185,6 +185,15 @@ struct Ctx {
   cudaEvent_t cev[2] = {nullptr, nullptr};   // coarse-solve batch markers
   double* h_done = nullptr;                  // pinned, 2 slots
   AdvData adv;
+  // the preconditioner step of a flexible-CG iteration (V-cycle, beta, direction)
+  // as a CUDA graph, captured on a library stream and replayed on the caller's
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pc_graph = nullptr;
+  const void* pc_graph_key[3] = {nullptr, nullptr, nullptr};   // w, sc, level-0 x the graph was captured with
+  int pc_graph_prec = -1;
+  uint64_t pc_graph_gen = 0;                 // pc_gen at capture
+  uint64_t pc_gen = 0;                       // bumped by every preconditioner set-up
+  bool pc_graph_off = false;                 // a capture failed: direct launches from then on
   // scratch of the whole-GPU coarse solve
   double* cg_part = nullptr;                 // [3 * COARSE_GRID_MAX]
   unsigned* cg_bar = nullptr;                // [COARSE_GRID_MAX + 1]

@@ -382,6 +382,8 @@ void sem_free(sem_ctx* h) {
   for (auto& e : C->cev)
     if (e) cudaEventDestroy(e);
   if (C->h_done) cudaFreeHost(C->h_done);
+  if (C->pc_graph) cudaGraphExecDestroy(C->pc_graph);
+  if (C->cap_stream) cudaStreamDestroy(C->cap_stream);
   delete C;
 }
 
@@ -504,6 +506,7 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   CUSTEP(cudaEventCreateWithFlags(&C->cev[0], cudaEventDisableTiming));
   CUSTEP(cudaEventCreateWithFlags(&C->cev[1], cudaEventDisableTiming));
   CUSTEP(cudaMallocHost((void**)&C->h_done, 2 * sizeof(double)));
+  CUSTEP(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking));
   CUSTEP(cudaStreamSynchronize(s));
   cudaStreamDestroy(s);
 #undef STEP

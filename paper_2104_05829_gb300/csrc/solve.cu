@@ -313,6 +313,7 @@ int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
     return SEM_EINVAL;
   }
   C.pc_ready = false;
+  ++C.pc_gen;
   for (int l = 0; l < C.nlevels; ++l) {
     Level& L = C.lev[l];
     SEM_TRY(level_dinv(C, l, h1, h2, nullptr, L.dinv, L.dinv32, s));
@@ -335,6 +336,56 @@ int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
   C.pc_h2 = h2;
   C.pc_prec = prec;
   C.pc_ready = true;
+  return SEM_OK;
+}
+
+// Preconditioner step of a flexible-CG iteration: z = V-cycle(r) (input already in
+// the finest level's b, output in its x), beta and the new direction. After the
+// first call with given pointers it is captured once on the library's capture
+// stream and replayed as a CUDA graph on s (about 45 launches become one). The
+// caller runs the same step directly at least once before (the first V-cycle of
+// the solve), so one-time set-up calls never happen inside a capture. A capture
+// that fails (a coarse execution that waits on the host, say) switches the
+// context to direct launches.
+int precond_step(Ctx& C, int prec, const void* zx, int zprec, const double* w, double* sc, cudaStream_t s) {
+  const Level& L = C.lev[0];
+  auto direct = [&](cudaStream_t st) -> int {
+    SEM_TRY(vcycle_level(C, 0, prec, st));
+    SEM_TRY(kr_beta_flex(C, L, zx, zprec, C.r, w, sc, st));
+    return kr_direction(L, C.p, zx, zprec, sc, st);
+  };
+  if (C.pc_graph_off || !C.cap_stream) return direct(s);
+  const bool match = C.pc_graph && C.pc_graph_prec == prec && C.pc_graph_gen == C.pc_gen &&
+                     C.pc_graph_key[0] == w && C.pc_graph_key[1] == sc && C.pc_graph_key[2] == zx;
+  if (!match) {
+    if (C.pc_graph) {
+      cudaGraphExecDestroy(C.pc_graph);
+      C.pc_graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(C.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      C.pc_graph_off = true;
+      return direct(s);
+    }
+    const int rc = direct(C.cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(C.cap_stream, &g);
+    cudaError_t ei = cudaErrorUnknown;
+    if (rc == SEM_OK && e == cudaSuccess && g) ei = cudaGraphInstantiate(&C.pc_graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      C.pc_graph = nullptr;
+      C.pc_graph_off = true;
+      return direct(s);
+    }
+    C.pc_graph_prec = prec;
+    C.pc_graph_gen = C.pc_gen;
+    C.pc_graph_key[0] = w;
+    C.pc_graph_key[1] = sc;
+    C.pc_graph_key[2] = zx;
+  }
+  SEM_CUDA_TRY(cudaGraphLaunch(C.pc_graph, s));
   return SEM_OK;
 }
 
@@ -724,9 +775,7 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
           break;
         }
         if (hs[S_DONE] != 0.0) break;
-        SEM_TRY(vcycle_level(*C, 0, prec, s));
-        SEM_TRY(kr_beta_flex(*C, L, v0.x, vp, C->r, w, sc, s));
-        SEM_TRY(kr_direction(L, C->p, v0.x, vp, sc, s));
+        SEM_TRY(precond_step(*C, prec, v0.x, vp, w, sc, s));
       }
       if (rc == SEM_OK && C->h_scal[S_DONE] == 0.0) rc = SEM_ENOTCONV;
     }
