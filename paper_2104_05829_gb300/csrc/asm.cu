@@ -191,6 +191,11 @@ __device__ __forceinline__ int layer_slot(int f, int a, int b) {
   return kb * Sh::PS + jb * Sh::RS + ib;
 }
 
+// quotient for the eigenvalue scaling: IEEE division in FP64, the fast single-precision
+// division (about 2 ulp) in FP32, where the local solves are a smoother anyway
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+
 // Row q of a matrix with row stride MR (a multiple of 4), loaded four entries at a time.
 template <typename T, int M, int MR>
 __device__ __forceinline__ void load_row(const T* __restrict__ row, T (&r)[MR]) {
@@ -256,17 +261,44 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
   for (int q = tq; q < Sh::BS; q += M2) box[q] = T(0);
   __syncthreads();
   if (active) {
+    // every load of this thread's box values (own points, then face-layer indices and
+    // values) goes out before the first is used
+    constexpr int NO = (NP3 + M2 - 1) / M2, NF = (6 * NP2 + M2 - 1) / M2;
     const size_t eb = (size_t)e * NP3;
-    for (int q = tq; q < NP3; q += M2) {
-      const int k = q / NP2, j = (q / NP) % NP, i = q % NP;
-      box[(k + 1) * PS + (j + 1) * RS + i + 1] = wv ? bv[eb + q] - wv[eb + q] : bv[eb + q];
+    T ob[NO], ow[NO];
+#pragma unroll
+    for (int c = 0; c < NO; ++c) {
+      const int q = tq + c * M2;
+      ob[c] = q < NP3 ? bv[eb + q] : T(0);
+      ow[c] = (wv && q < NP3) ? wv[eb + q] : T(0);
     }
     const int32_t* lay = layer + (size_t)e * 6 * NP2;
-    for (int q = tq; q < 6 * NP2; q += M2) {
-      const int32_t src = lay[q];
-      if (src >= 0) {
+    int32_t src[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+      const int q = tq + c * M2;
+      src[c] = q < 6 * NP2 ? lay[q] : -1;
+    }
+    T fb[NF], fw[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+      fb[c] = src[c] >= 0 ? bv[src[c]] : T(0);
+      fw[c] = (wv && src[c] >= 0) ? wv[src[c]] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NO; ++c) {
+      const int q = tq + c * M2;
+      if (q < NP3) {
+        const int k = q / NP2, j = (q / NP) % NP, i = q % NP;
+        box[(k + 1) * PS + (j + 1) * RS + i + 1] = ob[c] - ow[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+      const int q = tq + c * M2;
+      if (src[c] >= 0) {
         const int f = q / NP2, ab = q - f * NP2;
-        box[layer_slot<NP>(f, ab / NP, ab % NP)] = wv ? bv[src] - wv[src] : bv[src];
+        box[layer_slot<NP>(f, ab / NP, ab % NP)] = fb[c] - fw[c];
       }
     }
   }
@@ -312,7 +344,7 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const T den = h1 * (lr + ls + St[M * Sh::MR + m] * st * st) + h2;
-      v[m] = den != T(0) ? c * v[m] / den : T(0);
+      v[m] = den != T(0) ? fdiv(c * v[m], den) : T(0);
     }
     line_bwd<T, M, Sh::MR>(St, v, line, PS);
   }
