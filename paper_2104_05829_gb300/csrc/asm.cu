@@ -140,8 +140,10 @@ struct AsmShape {
   static constexpr int BS = PS * M;                                    // box stride
   static constexpr int MR = (M + 3) / 4 * 4;                           // row stride of S (16-byte rows)
   static constexpr int REF = M * MR + MR;                              // S and lam of one side combination
-  static constexpr int EPB = (320 / M2) > 0 ? (320 / M2) : 1;          // elements per block
-  static constexpr int THREADS = EPB * M2;
+  static constexpr int LPT = (M % 2 == 0) ? 2 : 1;                     // box lines per thread
+  static constexpr int TPE = M2 / LPT;                                 // threads per element
+  static constexpr int EPB = (320 / TPE) > 0 ? (320 / TPE) : 1;        // elements per block
+  static constexpr int THREADS = EPB * TPE;
 };
 
 // Blocks per SM requested from the register allocator: about 64 registers per
@@ -212,33 +214,42 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, T (&r)[MR]) 
   }
 }
 
-// Forward pass on one box line (base b, stride st): out[a] = sum_m S[m][a] line[m],
-// streaming row m of S (stride MR) and the line value from shared memory.
-template <typename T, int M, int MR>
-__device__ __forceinline__ void line_fwd(const T* __restrict__ S, const T* line, int st, T (&out)[M]) {
+// Forward pass on L box lines (bases line[c], common stride st): out[c][a] =
+// sum_m S[m][a] line_c[m], streaming row m of S (stride MR) once for all L lines.
+template <typename T, int M, int MR, int L>
+__device__ __forceinline__ void lines_fwd(const T* __restrict__ S, T* const (&line)[L], int st, T (&out)[L][M]) {
 #pragma unroll
-  for (int a = 0; a < M; ++a) out[a] = T(0);
+  for (int c = 0; c < L; ++c)
+#pragma unroll
+    for (int a = 0; a < M; ++a) out[c][a] = T(0);
 #pragma unroll 2
   for (int m = 0; m < M; ++m) {
-    const T v = line[m * st];
+    T v[L];
+#pragma unroll
+    for (int c = 0; c < L; ++c) v[c] = line[c][m * st];
     T r[MR];
     load_row<T, M, MR>(S + m * MR, r);
 #pragma unroll
-    for (int a = 0; a < M; ++a) out[a] = fma(r[a], v, out[a]);
+    for (int c = 0; c < L; ++c)
+#pragma unroll
+      for (int a = 0; a < M; ++a) out[c][a] = fma(r[a], v[c], out[c][a]);
   }
 }
 
-// Backward pass: line[a] = sum_m S[a][m] in[m], written straight to shared memory.
-template <typename T, int M, int MR>
-__device__ __forceinline__ void line_bwd(const T* __restrict__ S, const T (&in)[M], T* line, int st) {
+// Backward pass: line_c[a] = sum_m S[a][m] in[c][m], written straight to shared memory.
+template <typename T, int M, int MR, int L>
+__device__ __forceinline__ void lines_bwd(const T* __restrict__ S, const T (&in)[L][M], T* const (&line)[L], int st) {
 #pragma unroll 2
   for (int a = 0; a < M; ++a) {
     T r[MR];
     load_row<T, M, MR>(S + a * MR, r);
-    T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < M; ++m) acc = fma(r[m], in[m], acc);
-    line[a * st] = acc;
+    for (int c = 0; c < L; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < M; ++m) acc = fma(r[m], in[c][m], acc);
+      line[c][a * st] = acc;
+    }
   }
 }
 
@@ -248,27 +259,27 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
               const uint8_t* __restrict__ bt, const T* __restrict__ len, const T* __restrict__ ref, T h1, T h2,
               T* __restrict__ z, T* __restrict__ zf) {
   using Sh = AsmShape<NP>;
-  constexpr int M = Sh::M, M2 = Sh::M2, RS = Sh::RS, PS = Sh::PS, EPB = Sh::EPB;
+  constexpr int M = Sh::M, RS = Sh::RS, PS = Sh::PS, EPB = Sh::EPB, LPT = Sh::LPT, TPE = Sh::TPE;
   constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
   __shared__ __align__(16) T s_ref[9 * Sh::REF];
   __shared__ T s_box[EPB * Sh::BS];
   for (int q = threadIdx.x; q < 9 * Sh::REF; q += blockDim.x) s_ref[q] = ref[q];
-  const int le = threadIdx.x / M2;
-  const int tq = threadIdx.x - le * M2;
+  const int le = threadIdx.x / TPE;
+  const int tq = threadIdx.x - le * TPE;
   const int e = blockIdx.x * EPB + le;
   const bool active = e < E;
   T* box = s_box + le * Sh::BS;
-  for (int q = tq; q < Sh::BS; q += M2) box[q] = T(0);
+  for (int q = tq; q < Sh::BS; q += TPE) box[q] = T(0);
   __syncthreads();
   if (active) {
     // every load of this thread's box values (own points, then face-layer indices and
     // values) goes out before the first is used
-    constexpr int NO = (NP3 + M2 - 1) / M2, NF = (6 * NP2 + M2 - 1) / M2;
+    constexpr int NO = (NP3 + TPE - 1) / TPE, NF = (6 * NP2 + TPE - 1) / TPE;
     const size_t eb = (size_t)e * NP3;
     T ob[NO], ow[NO];
 #pragma unroll
     for (int c = 0; c < NO; ++c) {
-      const int q = tq + c * M2;
+      const int q = tq + c * TPE;
       ob[c] = q < NP3 ? bv[eb + q] : T(0);
       ow[c] = (wv && q < NP3) ? wv[eb + q] : T(0);
     }
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
     int32_t src[NF];
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
-      const int q = tq + c * M2;
+      const int q = tq + c * TPE;
       src[c] = q < 6 * NP2 ? lay[q] : -1;
     }
     T fb[NF], fw[NF];
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
     }
 #pragma unroll
     for (int c = 0; c < NO; ++c) {
-      const int q = tq + c * M2;
+      const int q = tq + c * TPE;
       if (q < NP3) {
         const int k = q / NP2, j = (q / NP) % NP, i = q % NP;
         box[(k + 1) * PS + (j + 1) * RS + i + 1] = ob[c] - ow[c];
@@ -295,7 +306,7 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
     }
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
-      const int q = tq + c * M2;
+      const int q = tq + c * TPE;
       if (src[c] >= 0) {
         const int f = q / NP2, ab = q - f * NP2;
         box[layer_slot<NP>(f, ab / NP, ab % NP)] = fb[c] - fw[c];
@@ -303,7 +314,8 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
     }
   }
   __syncthreads();
-  const int p = tq % M, q = tq / M;
+  // this thread's lines: (p, q0 + c M / LPT), c < LPT
+  const int p = tq % M, q0 = tq / M;
   int cr = 0, cs = 0, ct = 0;
   T sr = T(1), ss = T(1), st = T(1);
   if (active) {
@@ -318,61 +330,71 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
   const T* Sr = s_ref + cr * Sh::REF;
   const T* Ss = s_ref + cs * Sh::REF;
   const T* St = s_ref + ct * Sh::REF;
-  T v[M];
-  // forward r: line along i at (j, k) = (p, q)
-  {
-    T* line = box + q * PS + p * RS;
-    line_fwd<T, M, Sh::MR>(Sr, line, 1, v);
+  T v[LPT][M];
+  T* ln[LPT];
+  // forward r: lines along i at (j, k) = (p, q)
 #pragma unroll
-    for (int m = 0; m < M; ++m) line[m] = v[m];
-  }
+  for (int c = 0; c < LPT; ++c) ln[c] = box + (q0 + c * (M / LPT)) * PS + p * RS;
+  lines_fwd<T, M, Sh::MR, LPT>(Sr, ln, 1, v);
+#pragma unroll
+  for (int c = 0; c < LPT; ++c)
+#pragma unroll
+    for (int m = 0; m < M; ++m) ln[c][m] = v[c][m];
   __syncthreads();
-  // forward s: line along j at (i, k) = (p, q)
-  {
-    T* line = box + q * PS + p;
-    line_fwd<T, M, Sh::MR>(Ss, line, RS, v);
+  // forward s: lines along j at (i, k) = (p, q)
 #pragma unroll
-    for (int m = 0; m < M; ++m) line[m * RS] = v[m];
-  }
+  for (int c = 0; c < LPT; ++c) ln[c] = box + (q0 + c * (M / LPT)) * PS + p;
+  lines_fwd<T, M, Sh::MR, LPT>(Ss, ln, RS, v);
+#pragma unroll
+  for (int c = 0; c < LPT; ++c)
+#pragma unroll
+    for (int m = 0; m < M; ++m) ln[c][m * RS] = v[c][m];
   __syncthreads();
-  // t: forward, eigenvalue scaling, backward, on the line along k at (i, j) = (p, q)
-  {
-    T* line = box + q * RS + p;
-    line_fwd<T, M, Sh::MR>(St, line, PS, v);
-    const T lr = Sr[M * Sh::MR + p] * sr * sr, ls = Ss[M * Sh::MR + q] * ss * ss;
-    const T c = sr * ss * st;
+  // t: forward, eigenvalue scaling, backward, on the lines along k at (i, j) = (p, q)
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const T den = h1 * (lr + ls + St[M * Sh::MR + m] * st * st) + h2;
-      v[m] = den != T(0) ? fdiv(c * v[m], den) : T(0);
+  for (int c = 0; c < LPT; ++c) ln[c] = box + (q0 + c * (M / LPT)) * RS + p;
+  lines_fwd<T, M, Sh::MR, LPT>(St, ln, PS, v);
+  {
+    const T lr = Sr[M * Sh::MR + p] * sr * sr;
+    const T cc = sr * ss * st;
+#pragma unroll
+    for (int c = 0; c < LPT; ++c) {
+      const T ls = Ss[M * Sh::MR + q0 + c * (M / LPT)] * ss * ss;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const T den = h1 * (lr + ls + St[M * Sh::MR + m] * st * st) + h2;
+        v[c][m] = den != T(0) ? fdiv(cc * v[c][m], den) : T(0);
+      }
     }
-    line_bwd<T, M, Sh::MR>(St, v, line, PS);
   }
+  lines_bwd<T, M, Sh::MR, LPT>(St, v, ln, PS);
   __syncthreads();
   // backward s
-  {
-    T* line = box + q * PS + p;
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = line[m * RS];
-    line_bwd<T, M, Sh::MR>(Ss, v, line, RS);
+  for (int c = 0; c < LPT; ++c) {
+    ln[c] = box + (q0 + c * (M / LPT)) * PS + p;
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[c][m] = ln[c][m * RS];
   }
+  lines_bwd<T, M, Sh::MR, LPT>(Ss, v, ln, RS);
   __syncthreads();
   // backward r
-  {
-    T* line = box + q * PS + p * RS;
 #pragma unroll
-    for (int m = 0; m < M; ++m) v[m] = line[m];
-    line_bwd<T, M, Sh::MR>(Sr, v, line, 1);
+  for (int c = 0; c < LPT; ++c) {
+    ln[c] = box + (q0 + c * (M / LPT)) * PS + p * RS;
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[c][m] = ln[c][m];
   }
+  lines_bwd<T, M, Sh::MR, LPT>(Sr, v, ln, 1);
   __syncthreads();
   if (!active) return;
   const size_t eb = (size_t)e * NP3;
-  for (int t = tq; t < NP3; t += M2) {
+  for (int t = tq; t < NP3; t += TPE) {
     const int k = t / NP2, j = (t / NP) % NP, i = t % NP;
     z[eb + t] = box[(k + 1) * PS + (j + 1) * RS + i + 1];
   }
   T* zfe = zf + (size_t)e * 6 * NP2;
-  for (int t = tq; t < 6 * NP2; t += M2) {
+  for (int t = tq; t < 6 * NP2; t += TPE) {
     const int f = t / NP2, ab = t - f * NP2;
     zfe[t] = box[layer_slot<NP>(f, ab / NP, ab % NP)];
   }
@@ -438,7 +460,7 @@ int launch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, d
   const T* len = std::is_same<T, double>::value ? (const T*)L.sch_len : (const T*)L.sch_len32;
   const T* ref = std::is_same<T, double>::value ? (const T*)L.sch_ref : (const T*)L.sch_ref32;
   const unsigned grid = (unsigned)((L.E + Sh::EPB - 1) / Sh::EPB);
-  k_asm_fdm<T, NP><<<grid, Sh::EPB * Sh::M2, 0, s>>>(L.E, b, w, L.sch_layer, L.sch_bt, len, ref, (T)h1, (T)h2, z, zf);
+  k_asm_fdm<T, NP><<<grid, Sh::THREADS, 0, s>>>(L.E, b, w, L.sch_layer, L.sch_bt, len, ref, (T)h1, (T)h2, z, zf);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
