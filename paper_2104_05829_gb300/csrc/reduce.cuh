@@ -54,7 +54,16 @@ __device__ void reduce_finish(Sums<NS> a, double* part, unsigned* ticket, Fin fi
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     double t = 0;
-    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += __ldcg(part + s * gridDim.x + q);
+    for (unsigned q0 = threadIdx.x; q0 < gridDim.x; q0 += blockDim.x * 8) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const unsigned q = q0 + blockDim.x * k;
+        v[k] = q < gridDim.x ? __ldcg(part + s * gridDim.x + q) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += v[k];
+    }
     b.v[s] = t;
   }
   warp_sum(b);

@@ -200,7 +200,9 @@ struct Ctx {
   int* cg_err = nullptr;                     // [1]
 };
 
-constexpr int RED_BLOCKS = 304;   // 2 per SM on a 152-SM GB300; fixed for determinism
+// 8 per SM on a 152-SM GB300 (64 warps: enough loads in flight while warps wait on
+// the narrow FP64 pipe); fixed for determinism
+constexpr int RED_BLOCKS = 1216;
 constexpr int RED_THREADS = 256;
 
 // ---- ax.cu
