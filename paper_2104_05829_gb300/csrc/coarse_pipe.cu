@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
 #pragma unroll
   for (int c = 0; c < NPT; ++c) w[c] = gather(c, epoch);
 
-  // scalar state, held by thread 0
+  // scalar state, held by the first lane of the first totals warp
   double bb = 0, tol2 = 0, den_old = 0, rr = 0;
   int flag = 0, it = 0;
   for (int pass = 0;; ++pass) {
@@ -498,7 +498,10 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
         }
       }
     }
-    if (threadIdx.x == 32 * (PW - 4) && pass > 0) s_rgam = 1.0 / s_gam;
+    if (warp == PW - 4) {
+      if (lane == 0 && pass > 0) s_rgam = 1.0 / s_gam;
+      asm volatile("bar.arrive 1, 128;" ::: "memory");   // s_rgam is visible to the scalar step
+    }
     T nv[NPT];
 #pragma unroll
     for (int c = 0; c < NPT; ++c) nv[c] = gather(c, epoch);
@@ -522,9 +525,11 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) s_tot[tw] = v;
+      // the totals warps and the 1/gamma warp meet here; the scalar step then runs
+      // while the other warps still wait on their gathers
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 32 * (PW - 3)) {
       const double gnew = s_tot[0], del = s_tot[1];
       rr = s_tot[2];
       if (pass == 0) {
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
       s_al = alpha;
       s_be = (T)beta;
     }
-    __syncthreads();
+    __syncthreads();   // the gathers are done and the scalars are visible
     flag = s_flag;
     if (flag != 0) break;
     const T al = s_al, be = s_be;
@@ -577,7 +582,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   T* xg = static_cast<T*>(a.x);
   for (int bp = threadIdx.x; bp < npt; bp += PT)
     xg[(int64_t)s_el[bp >> 3] * NPC3 + (bp & 7)] = s_m[s_p2n[bp] & NODE_MASK];
-  if (bk == 0 && threadIdx.x == 0) {
+  if (bk == 0 && threadIdx.x == 32 * (PW - 3)) {
     a.sc[S_ITER] = it;
     a.sc[S_TOTAL] += it;
     a.sc[S_RR] = rr;
