@@ -31,15 +31,13 @@
 // decisions. The scalar step runs on one thread and keeps its FP64 work short
 // (GB300's FP64 pipe is narrow): 1 / gamma_old is formed earlier by another
 // thread, and the FP32 solve divides in FP32.
-// Exchange: the FP32 and BF16-factor solves publish each interface output and
-// each block partial as one 64-bit word holding the FP32 value and its epoch
-// (relaxed 64-bit accesses are single-copy atomic), and a block waits only on
-// the words it reads, with no fence and no grid barrier. The FP64 solve
-// publishes plain values, then a block publishes the epoch in its own flag
-// (release) and the first warp of every block waits for all flags (acquire).
-// Exchange buffer and partials are double-buffered by epoch parity: the dot
-// products couple every block once per iteration, so no block can overwrite a
-// word another block has still to read. Waits are bounded (about a second of SM
+// Exchange: every block publishes each interface output and each block partial
+// as tagged words (an FP32 value and its epoch in one 64-bit word; an FP64 value
+// as two such words, one per half, in one 128-bit access; relaxed 64-bit accesses
+// are single-copy atomic), and a block waits only on the words it reads, with no
+// fence and no grid barrier. Exchange buffer and partials are double-buffered by
+// epoch parity: the dot products couple every block once per iteration, so no
+// block can overwrite a word another block has still to read. Waits are bounded (about a second of SM
 // clock); after a timeout every wait ends at once and the solve reports a
 // breakdown.
 #include <algorithm>
@@ -67,7 +65,7 @@ struct PipeArgs {
   const void* b;
   void* x;
   const void* dinv;
-  void* xbuf;                       // [2][nL] in the arithmetic type
+  void* xbuf;                       // [2][nL] tagged values (8 bytes each in FP32, 16 in FP64)
   int64_t nL;
   const int32_t* el_off;
   const int32_t* el;
@@ -80,8 +78,7 @@ struct PipeArgs {
   int max_el, max_nd, max_cp;
   double h1, h2, tol;
   int maxit;
-  double* part;                     // [2][3][B]
-  unsigned* flags;                  // [B], zero before the launch
+  double* part;                     // [2][3][B] tagged partials
   int* err;
   double* sc;                       // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
 };
@@ -109,58 +106,6 @@ __device__ __forceinline__ double fval(double v) { return v; }
 __device__ __forceinline__ float fval(float v) { return v; }
 __device__ __forceinline__ float fval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-// All blocks have written what they publish for this epoch once this returns.
-// Release: the block barrier, then an acq_rel fence and the flag store by thread 0;
-// acquire: an acq_rel fence after the flags are seen, then the block barrier.
-// The first warp polls every block's flag, eight per lane per round trip. Waits
-// are bounded (about a second of SM clock); a wait that runs out, or that sees
-// another block's timeout, sets the global error flag and *s_err (shared), after
-// which this block waits no more.
-__device__ void sync_all(unsigned* flags, int* err, unsigned epoch, volatile int* s_err) {
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) {
-      fence_acq_rel_gpu();
-      *(volatile unsigned*)(flags + blockIdx.x) = epoch;
-    }
-    __syncwarp();
-    if (*s_err == 0) {
-      const unsigned G = gridDim.x;
-      const long long t0 = clock64();
-      for (unsigned q0 = threadIdx.x; q0 < G; q0 += 32 * 8) {
-        unsigned polls = 0;
-        while (true) {
-          unsigned v[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const unsigned q = q0 + 32 * k;
-            v[k] = q < G ? *(const volatile unsigned*)(flags + q) : epoch;
-          }
-          bool ok = true;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) ok = ok && v[k] >= epoch;
-          if (ok) break;
-          if ((++polls & 15u) == 0) {
-            if (*(volatile int*)err != 0) {
-              *s_err = 1;
-              break;
-            }
-            if (clock64() - t0 > (1ll << 31)) {
-              atomicExch(err, 1);
-              *s_err = 1;
-              break;
-            }
-          }
-        }
-      }
-    }
-    fence_acq_rel_gpu();
-  }
-  __syncthreads();
-}
-
 template <typename T>
 __device__ __forceinline__ T quotient(double n, double d);
 template <>
@@ -168,20 +113,49 @@ __device__ __forceinline__ double quotient<double>(double n, double d) { return 
 template <>
 __device__ __forceinline__ float quotient<float>(double n, double d) { return (float)n / (float)d; }
 
-// Tagged words of the FP32 exchange: the value's bits low, its epoch high. Relaxed
-// 64-bit accesses at GPU scope are single-copy atomic, so a reader that sees the
-// epoch it waits for holds that epoch's value; no fence or flag is needed.
-__device__ __forceinline__ void st_tagged(uint64_t* p, float v, unsigned tag) {
-  const uint64_t w = ((uint64_t)tag << 32) | __float_as_uint(v);
-  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
-}
-__device__ __forceinline__ uint64_t ld_tagged(const uint64_t* p) {
-  uint64_t w;
-  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
-  return w;
-}
+// Tagged words of the exchange. An FP32 value is one 64-bit word (value bits low,
+// epoch high); an FP64 value is two such words, one per 32-bit half, written and
+// read by one 128-bit access. Relaxed 64-bit accesses at GPU scope are single-copy
+// atomic, so a reader that sees the awaited epoch in every word of a value holds
+// that epoch's value; no fence and no flag are needed.
 __device__ __forceinline__ bool tag_is(uint64_t w, unsigned tag) { return (unsigned)(w >> 32) == tag; }
-__device__ __forceinline__ float tag_val(uint64_t w) { return __uint_as_float((unsigned)w); }
+__device__ __forceinline__ uint64_t tag_word(unsigned bits, unsigned tag) { return ((uint64_t)tag << 32) | bits; }
+
+template <typename T>
+struct Tagged;
+template <>
+struct Tagged<float> {
+  using W = uint64_t;
+  __device__ static void st(W* p, float v, unsigned tag) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(tag_word(__float_as_uint(v), tag)) : "memory");
+  }
+  __device__ static W ld(const W* p) {
+    W w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+  }
+  __device__ static W zero() { return 0; }
+  __device__ static bool ok(const W& w, unsigned tag) { return tag_is(w, tag); }
+  __device__ static float val(const W& w) { return __uint_as_float((unsigned)w); }
+};
+template <>
+struct Tagged<double> {
+  struct __align__(16) W {
+    uint64_t hi, lo;
+  };
+  __device__ static void st(W* p, double v, unsigned tag) {
+    const uint64_t a = tag_word((unsigned)__double2hiint(v), tag), b = tag_word((unsigned)__double2loint(v), tag);
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+  }
+  __device__ static W ld(const W* p) {
+    W w;
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(w.hi), "=l"(w.lo) : "l"(p) : "memory");
+    return w;
+  }
+  __device__ static W zero() { return {0, 0}; }
+  __device__ static bool ok(const W& w, unsigned tag) { return tag_is(w.hi, tag) && tag_is(w.lo, tag); }
+  __device__ static double val(const W& w) { return __hiloint2double((int)(unsigned)w.hi, (int)(unsigned)w.lo); }
+};
 
 // Bound of a wait on tagged words: go() is false once the wait has run about a
 // second of SM clock (then the global and block error flags are set) or another
@@ -208,12 +182,12 @@ struct SpinBound {
   }
 };
 
-// FP32 and BF16-factor solves (T = float) exchange tagged words and wait only on
-// the words they read; the FP64 solve publishes plain values and synchronises the
-// grid with sync_all.
+// Every block publishes tagged words and waits only on the words it reads.
 template <typename T, typename GT, int NPT, bool SMEM_G>
 __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
-  constexpr bool TAG = sizeof(T) == 4;
+  using TW = Tagged<T>;
+  using W = typename TW::W;
+  constexpr int GB = sizeof(T) == 8 ? 4 : 8;   // exchange words in flight per batch
   extern __shared__ __align__(16) unsigned char s_raw[];
   const PipeSmem lay = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp);
   GT* sG = reinterpret_cast<GT*>(s_raw);
@@ -236,9 +210,8 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   const GT* G = static_cast<const GT*>(a.G);
   const T* bv = static_cast<const T*>(a.b);
   const T* dv = static_cast<const T*>(a.dinv);
-  T* xbuf = static_cast<T*>(a.xbuf);                        // [2][nL] values (FP64 solve)
-  uint64_t* xtag = static_cast<uint64_t*>(a.xbuf);          // [2][nL] tagged words (FP32 solves)
-  uint64_t* ptag = reinterpret_cast<uint64_t*>(a.part);     // [2][3][B] tagged partials (FP32 solves)
+  W* xtag = static_cast<W*>(a.xbuf);                        // [2][nL] tagged values
+  W* ptag = reinterpret_cast<W*>(a.part);                   // [2][3][B] tagged partials
   if (threadIdx.x == 0) {
     s_err = 0;
     s_gam = 1.0;
@@ -327,8 +300,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
         s_pt[bp] = wv;
         if (pn < 0) {
           const size_t o = (size_t)(ep & 1u) * a.nL + (size_t)s_el[bp >> 3] * NPC3 + lq;
-          if constexpr (TAG) st_tagged(xtag + o, (float)wv, ep);
-          else __stcg(xbuf + o, wv);
+          TW::st(xtag + o, wv, ep);
         }
       }
       if (!SMEM_G) {
@@ -337,12 +309,9 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
       }
     }
   };
-  // all blocks' outputs of epoch ep are published (FP64: grid barrier; FP32: the
-  // block's own outputs are in shared memory, the rest is awaited word by word)
-  auto exchange = [&](unsigned ep) {
-    if constexpr (TAG) __syncthreads();
-    else sync_all(a.flags, a.err, ep, &s_err);
-  };
+  // the block's own outputs of epoch ep are in shared memory; the other blocks'
+  // are awaited word by word in the gathers
+  auto exchange = [&](unsigned) { __syncthreads(); };
   // assembled value of node slot c at epoch ep: every copy, in canonical order
   auto gather = [&](int c, unsigned ep) -> T {
     const int jn = threadIdx.x + c * PT;
@@ -351,19 +320,22 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
     const size_t base = (size_t)(ep & 1u) * a.nL;
     T v[8];
     if (m <= 8) {
-      if constexpr (TAG) {
-        int32_t lr[8];
-        uint64_t wd[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = T(0);
+      // the copies' words in batches of GB (registers: an FP64 word pair is 16 bytes)
+#pragma unroll
+      for (int h = 0; h < 8; h += GB) {
+        int32_t lr[GB];
+        W wd[GB];
         unsigned need = 0;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          v[t] = T(0);
+        for (int t = 0; t < GB; ++t) {
           lr[t] = 0;
-          wd[t] = 0;
-          if (t < m) {
-            const int32_t e = s_cp[q0 + t];
+          wd[t] = TW::zero();
+          if (h + t < m) {
+            const int32_t e = s_cp[q0 + h + t];
             if (e >= 0) {
-              v[t] = s_pt[e];
+              v[h + t] = s_pt[e];
             } else {
               lr[t] = -e - 1;
               need |= 1u << t;
@@ -371,29 +343,20 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
           }
         }
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
-          if ((need >> t) & 1u) wd[t] = ld_tagged(xtag + base + lr[t]);
+        for (int t = 0; t < GB; ++t)
+          if ((need >> t) & 1u) wd[t] = TW::ld(xtag + base + lr[t]);
         SpinBound sb;
         while (true) {
 #pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (((need >> t) & 1u) && tag_is(wd[t], ep)) {
-              v[t] = tag_val(wd[t]);
+          for (int t = 0; t < GB; ++t)
+            if (((need >> t) & 1u) && TW::ok(wd[t], ep)) {
+              v[h + t] = TW::val(wd[t]);
               need &= ~(1u << t);
             }
           if (need == 0 || !sb.go(a.err, &s_err)) break;
 #pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if ((need >> t) & 1u) wd[t] = ld_tagged(xtag + base + lr[t]);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          v[t] = T(0);
-          if (t < m) {
-            const int32_t e = s_cp[q0 + t];
-            v[t] = e >= 0 ? s_pt[e] : __ldcg(xbuf + base + (-(int64_t)e - 1));
-          }
+          for (int t = 0; t < GB; ++t)
+            if ((need >> t) & 1u) wd[t] = TW::ld(xtag + base + lr[t]);
         }
       }
       T sum = v[0];
@@ -408,14 +371,12 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
       T vt;
       if (e >= 0) {
         vt = s_pt[e];
-      } else if constexpr (TAG) {
-        const uint64_t* wp = xtag + base + (-(int64_t)e - 1);
-        uint64_t wd = ld_tagged(wp);
-        SpinBound sb;
-        while (!tag_is(wd, ep) && sb.go(a.err, &s_err)) wd = ld_tagged(wp);
-        vt = tag_val(wd);
       } else {
-        vt = __ldcg(xbuf + base + (-(int64_t)e - 1));
+        const W* wp = xtag + base + (-(int64_t)e - 1);
+        W wd = TW::ld(wp);
+        SpinBound sb;
+        while (!TW::ok(wd, ep) && sb.go(a.err, &s_err)) wd = TW::ld(wp);
+        vt = TW::val(wd);
       }
       sum = t == 0 ? vt : sum + vt;
     }
@@ -469,10 +430,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
         for (int o = PW / 2; o > 0; o >>= 1) v[t] += __shfl_xor_sync(0xffffffffu, v[t], o);
       }
       const T mine = lane == 0 ? v[0] : (lane == 1 ? v[1] : v[2]);
-      if (lane < 3) {
-        if constexpr (TAG) st_tagged(ptag + pbase + (size_t)lane * B + bk, (float)mine, epoch);
-        else __stcg(a.part + pbase + (size_t)lane * B + bk, (double)mine);
-      }
+      if (lane < 3) TW::st(ptag + pbase + (size_t)lane * B + bk, mine, epoch);
     }
     apply(epoch);
     exchange(epoch);
@@ -480,21 +438,18 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
     // (their loads go out before the gathers), a fourth lane forms 1 / gamma_old
     const int tw = warp - (PW - 3);
     double ld[8];
-    uint64_t wd[8];
+    W wd[GB];
     unsigned need = 0;
     if (tw >= 0) {
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
+      for (int kk = 0; kk < 8; ++kk) ld[kk] = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < GB; ++kk) {
         const int q = lane + 32 * kk;
-        ld[kk] = 0.0;
-        wd[kk] = 0;
+        wd[kk] = TW::zero();
         if (q < B) {
-          if constexpr (TAG) {
-            wd[kk] = ld_tagged(ptag + pbase + (size_t)tw * B + q);
-            need |= 1u << kk;
-          } else {
-            ld[kk] = __ldcg(a.part + pbase + (size_t)tw * B + q);
-          }
+          wd[kk] = TW::ld(ptag + pbase + (size_t)tw * B + q);
+          need |= 1u << kk;
         }
       }
     }
@@ -506,19 +461,32 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
 #pragma unroll
     for (int c = 0; c < NPT; ++c) nv[c] = gather(c, epoch);
     if (tw >= 0) {
-      if constexpr (TAG) {
+      // block partials lane + 32 k, k < 8 (B <= 256), GB words per round
+#pragma unroll
+      for (int h = 0; h < 8; h += GB) {
+        if (h > 0) {
+          need = 0;
+#pragma unroll
+          for (int kk = 0; kk < GB; ++kk) {
+            const int q = lane + 32 * (h + kk);
+            if (q < B) {
+              wd[kk] = TW::ld(ptag + pbase + (size_t)tw * B + q);
+              need |= 1u << kk;
+            }
+          }
+        }
         SpinBound sb;
         while (true) {
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            if (((need >> kk) & 1u) && tag_is(wd[kk], epoch)) {
-              ld[kk] = (double)tag_val(wd[kk]);
+          for (int kk = 0; kk < GB; ++kk)
+            if (((need >> kk) & 1u) && TW::ok(wd[kk], epoch)) {
+              ld[h + kk] = (double)TW::val(wd[kk]);
               need &= ~(1u << kk);
             }
           if (need == 0 || !sb.go(a.err, &s_err)) break;
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk)
-            if ((need >> kk) & 1u) wd[kk] = ld_tagged(ptag + pbase + (size_t)tw * B + lane + 32 * kk);
+          for (int kk = 0; kk < GB; ++kk)
+            if ((need >> kk) & 1u) wd[kk] = TW::ld(ptag + pbase + (size_t)tw * B + lane + 32 * (h + kk));
         }
       }
       double v = ((ld[0] + ld[1]) + (ld[2] + ld[3])) + ((ld[4] + ld[5]) + (ld[6] + ld[7]));
@@ -784,8 +752,9 @@ int coarse_pipe_build(Level& L, cudaStream_t s) {
   SEM_TRY(upload(&L.pp_nd_fl, h.nd_fl, s));
   SEM_TRY(upload(&L.pp_cp_off, h.cp_off, s));
   SEM_TRY(upload(&L.pp_cp, h.cp, s));
-  if (cudaMalloc((void**)&L.pp_xbuf, 2 * (size_t)nL * sizeof(double) + 16) != cudaSuccess ||
-      cudaMalloc((void**)&L.pp_part, 6 * (size_t)B * sizeof(double) + 16) != cudaSuccess) {
+  // room for FP64 values: two tagged 64-bit words each
+  if (cudaMalloc((void**)&L.pp_xbuf, 4 * (size_t)nL * sizeof(double) + 16) != cudaSuccess ||
+      cudaMalloc((void**)&L.pp_part, 12 * (size_t)B * sizeof(double) + 16) != cudaSuccess) {
     cudaGetLastError();
     set_detail("cudaMalloc failed (sub-domain coarse solve)");
     return SEM_ENOMEM;
@@ -818,12 +787,11 @@ int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool
   a.G = G;
   Mat64 D = L.D;
   void* args[] = {&a, &D};
-  SEM_CUDA_TRY(cudaMemsetAsync(a.flags, 0, (size_t)L.pp_blocks * sizeof(unsigned), s));
   SEM_CUDA_TRY(cudaMemsetAsync(a.err, 0, sizeof(int), s));
-  if (sizeof(T) == 4) {   // tagged exchange: epochs start at 1, so no stale word matches
-    SEM_CUDA_TRY(cudaMemsetAsync(a.xbuf, 0, 2 * (size_t)L.nL * sizeof(uint64_t), s));
-    SEM_CUDA_TRY(cudaMemsetAsync(a.part, 0, 6 * (size_t)L.pp_blocks * sizeof(uint64_t), s));
-  }
+  // epochs start at 1, so no stale word of an earlier launch can match
+  using W = typename Tagged<T>::W;
+  SEM_CUDA_TRY(cudaMemsetAsync(a.xbuf, 0, 2 * (size_t)L.nL * sizeof(W), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(a.part, 0, 6 * (size_t)L.pp_blocks * sizeof(W), s));
   SEM_CUDA_TRY(cudaLaunchCooperativeKernel(f, dim3(L.pp_blocks), dim3(PT), args, smem, s));
   *used = true;
   return SEM_OK;
@@ -848,9 +816,9 @@ int launch_pipe(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, boo
 }  // namespace
 
 // Pipelined sub-domain coarse solve at order 1 (FP64, FP32 or BF16-factor V-cycles);
-// *used = false when it does not apply. bar: [COARSE_GRID_MAX] flags, err: [1].
+// *used = false when it does not apply. err: [1].
 int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
-                      double tol, int maxit, double* sc, unsigned* bar, int* err, cudaStream_t s, bool* used) {
+                      double tol, int maxit, double* sc, int* err, cudaStream_t s, bool* used) {
   *used = false;
   if (L.NP != NPC) return SEM_OK;
   SEM_TRY(coarse_pipe_build(L, s));
@@ -880,7 +848,6 @@ int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* di
   a.tol = tol;
   a.maxit = maxit;
   a.part = L.pp_part;
-  a.flags = bar;
   a.err = err;
   a.sc = sc;
   if (prec == SEM_FP64) return launch_pipe<double, double>(L, L.G, a, nsm, s, used);

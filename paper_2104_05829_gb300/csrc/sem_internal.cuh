@@ -126,8 +126,8 @@ struct Level {
   uint8_t* pp_nd_fl = nullptr;    // bit 0: the sub-domain holds the owner copy; bit 1: Dirichlet
   int32_t* pp_cp_off = nullptr;   // [nodes + 1] offsets into pp_cp
   int32_t* pp_cp = nullptr;       // copies in canonical order: >= 0 sub-domain point, < 0 -(local point + 1)
-  double* pp_xbuf = nullptr;      // [2][nL] exchange buffer (FP64 values, or tagged FP32 words)
-  double* pp_part = nullptr;      // [2][3][B] block partials (FP64, or tagged FP32 words)
+  double* pp_xbuf = nullptr;      // [2][nL] exchange buffer of tagged words (16 bytes per value)
+  double* pp_part = nullptr;      // [2][3][B] tagged block partials (16 bytes each)
 };
 
 // Device scalar slots (double) used by the Krylov kernels.
@@ -234,7 +234,7 @@ int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p,
 // ---- coarse_pipe.cu: one-launch pipelined coarse Jacobi-PCG on sub-domains (cooperative launch)
 int coarse_pipe_build(Level& L, cudaStream_t s);
 int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
-                      double tol, int maxit, double* sc, unsigned* bar, int* err, cudaStream_t s, bool* used);
+                      double tol, int maxit, double* sc, int* err, cudaStream_t s, bool* used);
 
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);

@@ -242,7 +242,7 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   const int mode = C.opts.coarse_mode;
   if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_PIPE)
     SEM_TRY(coarse_pipe_solve(L, prec, b, x, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol, C.opts.coarse_maxit, sc,
-                              C.cg_bar, C.cg_err, s, &used));
+                              C.cg_err, s, &used));
   if (used) return SEM_OK;
   if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_GRID)
     SEM_TRY(coarse_grid_solve(L, prec, b, x, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
