@@ -250,8 +250,9 @@ def solve_bench(ctx_cls, args, dev):
     stream = torch.cuda.current_stream()
     variants = (("fp64", "fp64", False, "jacobi"), ("fp32", "fp32", False, "jacobi"),
                 ("bf16g", "bf16g", False, "jacobi"), ("fp32_outer_pairs", "fp32", True, "jacobi"),
+                ("bf16g_outer_pairs", "bf16g", True, "jacobi"),
                 ("asm_fp64", "fp64", False, "asm"), ("asm_fp32", "fp32", False, "asm"),
-                ("asm_fp32_outer_pairs", "fp32", True, "asm"))
+                ("asm_fp32_outer_pairs", "fp32", True, "asm"), ("asm_bf16g_outer_pairs", "bf16g", True, "asm"))
     if args.solve_variants:
         keep = set(args.solve_variants.split(","))
         variants = tuple(v for v in variants if v[0] in keep)
