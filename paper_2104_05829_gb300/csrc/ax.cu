@@ -144,10 +144,10 @@ int launch_ax(const Level& L, const T* u, T* w, const GT* G, const typename MatT
 
 // --------------------------------------------------------------------------
 // The same operator in FP32 arithmetic with the factors staged by bulk copies:
-// thread 0 starts one cp.async.bulk per element of the block (its 7 NP^3 factor
-// values are contiguous) on an mbarrier before the threads load u, so a block
-// has all of its factor bytes in flight at once; the contractions then read G
-// and B from shared memory. The FP32 operator moves u, G, B and w and does
+// thread 0 starts one cp.async.bulk for the block's u (contiguous) and one per
+// element for its 7 NP^3 factor values on an mbarrier, so a block has all of its
+// input bytes in flight at once; the contractions then read u, G and B from
+// shared memory. The FP32 operator moves u, G, B and w and does
 // little arithmetic per byte, so it is bound by HBM and wants many bytes in
 // flight. Two elements per block keep five blocks on an SM at N = 7. Measured
 // at N = 7 on the 24^3 box: 70 us -> 46 us per application (81 % of the HBM
@@ -167,9 +167,13 @@ template <typename GT, int NP>
 __host__ __device__ constexpr size_t bulk_g_bytes() {
   return ((size_t)bulk_epb<NP>() * 7 * NP * NP * NP * sizeof(GT) + 127) / 128 * 128;
 }
+template <int NP>
+__host__ __device__ constexpr size_t bulk_u_bytes() {
+  return ((size_t)bulk_epb<NP>() * NP * NP * NP * sizeof(float) + 127) / 128 * 128;
+}
 template <typename GT, int NP>
 __host__ __device__ constexpr size_t bulk_smem() {
-  return bulk_g_bytes<GT, NP>() + (size_t)3 * bulk_epb<NP>() * Pad<NP>::ES * sizeof(float);
+  return bulk_g_bytes<GT, NP>() + bulk_u_bytes<NP>() + (size_t)2 * bulk_epb<NP>() * Pad<NP>::ES * sizeof(float);
 }
 
 template <typename GT, int NP, bool VARH1>
@@ -183,8 +187,8 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
   if (skip && *skip != 0.0) return;
   extern __shared__ __align__(128) unsigned char s_raw[];
   GT* sG = reinterpret_cast<GT*>(s_raw);                                   // [EPB][7][NP3]
-  T* s_u = reinterpret_cast<T*>(s_raw + bulk_g_bytes<GT, NP>());          // [EPB][ES] padded
-  T* s_r = s_u + EPB * ES;
+  T* s_u = reinterpret_cast<T*>(s_raw + bulk_g_bytes<GT, NP>());          // [EPB][NP3] as in HBM
+  T* s_r = reinterpret_cast<T*>(s_raw + bulk_g_bytes<GT, NP>() + bulk_u_bytes<NP>());   // [EPB][ES] padded
   T* s_s = s_r + EPB * ES;
   __shared__ T s_D[NP2];    // D[a][b] at a*NP + b
   __shared__ T s_Dt[NP2];   // D[a][b] at b*NP + a
@@ -200,7 +204,8 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
   const int nel = min(EPB, E - e0);
   if (tid == 0) {
     mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, (unsigned)(nel * GE * sizeof(GT)));
+    mbar_expect_tx(&bar, (unsigned)(nel * GE * sizeof(GT) + nel * NP3 * sizeof(T)));
+    bulk_g2s(s_u, u + (size_t)e0 * NP3, nel * NP3 * sizeof(T), &bar);
     for (int q = 0; q < nel; ++q) bulk_g2s(sG + q * GE, G + (size_t)(e0 + q) * GE, GE * sizeof(GT), &bar);
   }
   for (int t = tid; t < NP2; t += blockDim.x) {
@@ -208,25 +213,20 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
     s_Dt[(t % NP) * NP + t / NP] = Dm.a[t];
   }
   const bool active = e < E;
-  T* su = s_u + le * ES;
+  const T* su = s_u + le * NP3;   // unpadded (k, j, l) rows: conflict-free at N = 7 for both contractions
   T* sr = s_r + le * ES;
   T* ss = s_s + le * ES;
   T ru[NP];
   const size_t ebase = (size_t)e * NP3;
-  if (active) {
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      ru[k] = u[ebase + k * NP2 + ij];
-      su[k * PS + j * RS + i] = ru[k];
-    }
-  }
-  __syncthreads();   // s_u, s_D and the barrier's initialisation are visible
+  __syncthreads();   // s_D and the barrier's initialisation are visible
   if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
     if (active)
 #pragma unroll
       for (int k = 0; k < NP; ++k) w[ebase + k * NP2 + ij] = __int_as_float(0x7fc00000);
     return;
   }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) ru[k] = active ? su[k * NP2 + ij] : T(0);
   T wt[NP];
   if (active) {
     const GT* Ge = sG + le * GE + ij;
@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
       T ur = 0, us = 0, ut = 0;
 #pragma unroll
       for (int l = 0; l < NP; ++l) {
-        ur = fma(s_Dt[l * NP + i], su[k * PS + j * RS + l], ur);   // D[i][l] u[k][j][l]
-        us = fma(s_Dt[l * NP + j], su[k * PS + l * RS + i], us);   // D[j][l] u[k][l][i]
-        ut = fma(Dm.a[k * NP + l], ru[l], ut);                     // D[k][l] u[l][j][i]
+        ur = fma(s_Dt[l * NP + i], su[k * NP2 + j * NP + l], ur);   // D[i][l] u[k][j][l]
+        us = fma(s_Dt[l * NP + j], su[k * NP2 + l * NP + i], us);   // D[j][l] u[k][l][i]
+        ut = fma(Dm.a[k * NP + l], ru[l], ut);                      // D[k][l] u[l][j][i]
       }
       const int o = k * NP2;
       const T g11 = to_f(Ge[0 * NP3 + o]), g12 = to_f(Ge[1 * NP3 + o]), g13 = to_f(Ge[2 * NP3 + o]);
