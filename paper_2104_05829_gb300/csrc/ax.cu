@@ -150,14 +150,16 @@ int launch_ax(const Level& L, const T* u, T* w, const GT* G, const typename MatT
 // shared memory. The FP32 operator moves u, G, B and w and does
 // little arithmetic per byte, so it is bound by HBM and wants many bytes in
 // flight. Two elements per block keep five blocks on an SM at N = 7. Measured
-// at N = 7 on the 24^3 box: 70 us -> 46 us per application (81 % of the HBM
-// copy rate); at N = 3 the plain kernel is faster (its data fit in L2).
+// at N = 7 on the 24^3 box: 70 us -> 44 us per application (87 % of the HBM
+// copy rate).
 // A block whose copies have not landed after about a second writes NaN to its
 // outputs (the solvers report a breakdown) instead of waiting on.
 // --------------------------------------------------------------------------
 template <typename GT, int NP>
-__host__ __device__ constexpr bool bulk_ok() {   // orders 7, 9, 11 (lower orders' data sit in L2)
-  return NP >= 8 && NP % 2 == 0 && (7 * NP * NP * NP * sizeof(GT)) % 16 == 0;
+// orders 7, 9, 11 (at N = 3 the plain kernel measured 9.4 us against 10.9 us: its data
+// sit in L2, and two elements' worth of 16 threads per block starve the copies)
+__host__ __device__ constexpr bool bulk_ok() {
+  return NP >= 8 && NP % 2 == 0 && (7 * NP * NP * NP * sizeof(GT)) % 16 == 0 && (NP * NP * NP * 4) % 16 == 0;
 }
 template <int NP>
 __host__ __device__ constexpr int bulk_epb() {
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
     mbar_init(&bar, 1);
     mbar_expect_tx(&bar, (unsigned)(nel * GE * sizeof(GT) + nel * NP3 * sizeof(T)));
     bulk_g2s(s_u, u + (size_t)e0 * NP3, nel * NP3 * sizeof(T), &bar);
-    for (int q = 0; q < nel; ++q) bulk_g2s(sG + q * GE, G + (size_t)(e0 + q) * GE, GE * sizeof(GT), &bar);
+    bulk_g2s(sG, G + (size_t)e0 * GE, nel * GE * sizeof(GT), &bar);   // consecutive elements are contiguous
   }
   for (int t = tid; t < NP2; t += blockDim.x) {
     s_D[t] = Dm.a[t];
