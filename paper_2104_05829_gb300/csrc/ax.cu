@@ -156,8 +156,8 @@ int launch_ax(const Level& L, const T* u, T* w, const GT* G, const typename MatT
 // outputs (the solvers report a breakdown) instead of waiting on.
 // --------------------------------------------------------------------------
 template <typename GT, int NP>
-// orders 7, 9, 11 (at N = 3 the plain kernel measured 9.4 us against 10.9 us: its data
-// sit in L2, and two elements' worth of 16 threads per block starve the copies)
+// orders 7, 9, 11 (at N = 3 the plain kernel measured 9.4 us against 10.9 us: that
+// level's data sit in L2, where per-thread loads already have short latency)
 __host__ __device__ constexpr bool bulk_ok() {
   return NP >= 8 && NP % 2 == 0 && (7 * NP * NP * NP * sizeof(GT)) % 16 == 0 && (NP * NP * NP * 4) % 16 == 0;
 }
