@@ -75,8 +75,8 @@ extern "C" {
 #define SEM_COARSE_CLUSTER 1  /* FP32/BF16 V-cycles: one launch on one cluster, problem held on chip; else KERNELS */
 #define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches */
 #define SEM_COARSE_GRID 3     /* one cooperative launch over the whole GPU when it fits; else KERNELS */
-#define SEM_COARSE_PIPE 4     /* pipelined PCG on one sub-domain per SM, one cooperative launch with one
-                                 grid-wide synchronisation per iteration, when it fits; else KERNELS */
+#define SEM_COARSE_PIPE 4     /* pipelined PCG on one sub-domain per SM in one cooperative launch; blocks
+                                 exchange tagged words, no grid barrier; when it fits, else KERNELS */
 
 /* sem_solve preconditioners and flags */
 #define SEM_PC_JACOBI 0      /* Jacobi-PCG (the viscous-substep solver, Section 2.2) */

@@ -1,5 +1,5 @@
 // Coarsest-level Jacobi-PCG (order 1) as pipelined PCG on sub-domains, in one
-// cooperative launch with one grid-wide synchronisation per iteration.
+// cooperative launch with one exchange between blocks per iteration.
 //
 // The order-1 elements are split into one sub-domain per block by recursive
 // coordinate bisection of their centroids (host, once per level). A block keeps
@@ -10,15 +10,15 @@
 // operator output is a gather: every block sums, for each of its nodes, all
 // copies of the node in canonical order (ascending local index), its own copies
 // from shared memory and the other blocks' from an exchange buffer that those
-// blocks publish before the synchronisation. Nothing is scattered into another
-// block, so one synchronisation per operator application suffices.
+// blocks publish. Nothing is scattered into another block, so one exchange per
+// operator application suffices.
 //
 // The iteration is pipelined PCG (Ghysels and Vanroose, Parallel Computing
 // 2014) with the Jacobi preconditioner: the dot products of an iteration need
 // only vectors that exist before its operator application, so their block
-// partials travel with the same synchronisation. In exact arithmetic the
+// partials travel in the same exchange. In exact arithmetic the
 // iterates are those of Jacobi-PCG.
-//   r = b, u = D^-1 r, w = A u (one extra synchronisation); for i = 0, 1, ...
+//   r = b, u = D^-1 r, w = A u (one extra exchange); for i = 0, 1, ...
 //     gamma = (r, u), delta = (w, u), rr = (r, r); m = D^-1 w; n = A m
 //     stop if rr <= tol^2 (b, b) or i = maxit (x is the result)
 //     beta = gamma / gamma_old (0 at i = 0), pi = delta - beta^2 pi_old (= (p, A p)),
