@@ -275,7 +275,7 @@ def solve_bench(ctx_cls, args, dev):
         t = min(times)
         out[name] = {"time_to_1e-8_s": t, "median_s": statistics.median(times), "iters": info["iters"],
                      "ms_per_iter": 1e3 * t / max(1, info["iters"]), "relres": info["relres"],
-                     "coarse_iters": info["coarse_iters"], "smoother": f"cheby-{'asm' if sm == 'asm' else 'jac'} {prec}",
+                     "coarse_iters": info["coarse_iters"], "graph_steps": info["graph_steps"], "smoother": f"cheby-{'asm' if sm == 'asm' else 'jac'} {prec}",
                      "outer_operator": "f32x2" if op else "f64"}
     if args.jacobi:
         ctx.solve(b, tol=1e-8, maxit=20000, precond="jacobi", rhs="assembled")

@@ -139,6 +139,8 @@ typedef struct {
   double lmax[SEM_MAX_LEVELS]; /* Lanczos estimates of lambda_max(D^-1 A) per smoothed level */
   double relres0;            /* sem_solve_proj: ||b - A xbar|| / ||b|| after projection; else -1 */
   int32_t proj_count;        /* sem_solve_proj: basis size after the solve; else 0 */
+  int32_t graph_steps;       /* p-MG: preconditioner steps (V-cycle, beta, direction) replayed from a
+                                CUDA graph in this solve; 0 where the context launches them directly */
 } sem_info;
 
 /* Per-level sizes. */

@@ -52,7 +52,8 @@ class SemCoef(C.Structure):
 class SemInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double), ("bnorm", C.c_double),
                 ("coarse_iters", C.c_int32), ("nlevels", C.c_int32),
-                ("lmax", C.c_double * SEM_MAX_LEVELS), ("relres0", C.c_double), ("proj_count", C.c_int32)]
+                ("lmax", C.c_double * SEM_MAX_LEVELS), ("relres0", C.c_double), ("proj_count", C.c_int32),
+                ("graph_steps", C.c_int32)]
 
 
 class SemLevelDesc(C.Structure):

@@ -763,6 +763,7 @@ int coarse_pipe_build(Level& L, cudaStream_t s) {
   L.pp_max_el = h.max_el;
   L.pp_max_nd = h.max_nd;
   L.pp_max_cp = h.max_cp;
+  L.pp_nsm = nsm;
   L.pp_blocks = B;
   return SEM_OK;
 }
@@ -774,16 +775,27 @@ int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool
   const size_t smem = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp).total;
   if (smem > 220 * 1024) return SEM_OK;
   const void* f = (const void*)k_coarse_pipe<T, GT, NPT, SMEM_G>;
-  if (smem > 48 * 1024 && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return SEM_OK;
+  // the shared-memory attribute and the occupancy are asked once per size, so that a
+  // launch captured into a CUDA graph issues no such calls
+  static size_t attr_smem = 48 * 1024, occ_smem = 0;
+  static int occ_per_sm = 0;
+  if (smem > attr_smem) {
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return SEM_OK;
+    }
+    attr_smem = smem;
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, PT, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return SEM_OK;
+  if (occ_smem != smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, PT, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return SEM_OK;
+    }
+    occ_smem = smem;
+    occ_per_sm = per_sm;
   }
-  if (per_sm < 1 || L.pp_blocks > per_sm * nsm) return SEM_OK;
+  if (occ_per_sm < 1 || L.pp_blocks > occ_per_sm * nsm) return SEM_OK;
   a.G = G;
   Mat64 D = L.D;
   void* args[] = {&a, &D};
@@ -823,9 +835,7 @@ int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* di
   if (L.NP != NPC) return SEM_OK;
   SEM_TRY(coarse_pipe_build(L, s));
   if (L.pp_blocks < 1 || L.pp_blocks > PIPE_MAX_BLOCKS) return SEM_OK;
-  int dev = 0, nsm = 0;
-  SEM_CUDA_TRY(cudaGetDevice(&dev));
-  SEM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nsm = L.pp_nsm;   // read at build time: no device query inside a graph capture
   PipeArgs a{};
   a.b = b;
   a.x = x;

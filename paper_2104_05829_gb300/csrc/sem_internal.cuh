@@ -118,6 +118,7 @@ struct Level {
   // sub-domain coarse solve (coarse_pipe.cu; built on first use at order 1)
   int pp_blocks = 0;              // sub-domains, one block each; 0 not built, -1 does not apply
   int pp_max_el = 0, pp_max_nd = 0, pp_max_cp = 0;   // largest sub-domain: elements, nodes, copy entries
+  int pp_nsm = 0;                 // SMs of the device the sub-domains were built for
   int32_t* pp_el_off = nullptr;   // [B+1] offsets into pp_el
   int32_t* pp_el = nullptr;       // [E] elements grouped by sub-domain, ascending within one
   int32_t* pp_p2n = nullptr;      // [nL] per point in pp_el order: sub-domain node | bit 31 when published
@@ -194,6 +195,7 @@ struct Ctx {
   uint64_t pc_graph_gen = 0;                 // pc_gen at capture
   uint64_t pc_gen = 0;                       // bumped by every preconditioner set-up
   bool pc_graph_off = false;                 // a capture failed: direct launches from then on
+  int graph_steps = 0;                       // graph replays in the current solve
   // scratch of the whole-GPU coarse solve
   double* cg_part = nullptr;                 // [3 * COARSE_GRID_MAX]
   unsigned* cg_bar = nullptr;                // [COARSE_GRID_MAX + 1]

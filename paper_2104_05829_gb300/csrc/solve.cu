@@ -386,6 +386,7 @@ int precond_step(Ctx& C, int prec, const void* zx, int zprec, const double* w, d
     C.pc_graph_key[2] = zx;
   }
   SEM_CUDA_TRY(cudaGraphLaunch(C.pc_graph, s));
+  ++C.graph_steps;
   return SEM_OK;
 }
 
@@ -665,6 +666,7 @@ namespace {
 int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, int maxit, int precond, int prec,
                int rhs_flags, double* u, sem_info* info, cudaStream_t s) {
   SEM_TRY(check_level(C, 0));
+  C->graph_steps = 0;
   if (!f || !c || !u || f == u || !(tol >= 0.0) || maxit < 0 ||
       (precond != SEM_PC_JACOBI && precond != SEM_PC_PMG) ||
       (rhs_flags & ~(SEM_RHS_ASSEMBLED | SEM_X0_GIVEN | SEM_OUTER_PAIRS)) ||
@@ -813,6 +815,7 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
     for (int l = 0; l < SEM_MAX_LEVELS; ++l) info->lmax[l] = (l < C->nlevels) ? C->lev[l].lmax : 0.0;
     info->relres0 = relres0;
     info->proj_count = pcount;
+    info->graph_steps = C->graph_steps;
   }
   if (rc == SEM_ENOTCONV) set_detail("no convergence in %d iterations (relres %.3e)", maxit, bb > 0 ? std::sqrt(rr / bb) : 0.0);
   if (rc == SEM_EBREAKDOWN) set_detail("Krylov breakdown after %d iterations", iters);

@@ -275,7 +275,8 @@ class SemContext:
         else:
             rc = self._lib.sem_solve_proj(self._h, proj._h, *args)
         out = {"iters": info.iters, "relres": info.relres, "bnorm": info.bnorm, "coarse_iters": info.coarse_iters,
-               "lmax": [info.lmax[i] for i in range(max(0, info.nlevels - 1))], "status": rc}
+               "lmax": [info.lmax[i] for i in range(max(0, info.nlevels - 1))], "status": rc,
+               "graph_steps": info.graph_steps}
         if proj is not None:
             out["relres0"] = info.relres0
             out["proj_count"] = info.proj_count

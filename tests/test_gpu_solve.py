@@ -181,10 +181,12 @@ def test_pmg_solve_graph_replay_matches_direct_launches(smoother):
     x1, i1 = ctx.solve(b, tol=1e-9, maxit=200, precond="pmg", prec="fp64", rhs="assembled")
     x2, i2 = ctx.solve(b, tol=1e-9, maxit=200, precond="pmg", prec="fp64", rhs="assembled")
     assert i1["iters"] == i2["iters"] > 2
+    # every preconditioner step after the first V-cycle of a solve comes from the graph
+    assert i1["graph_steps"] == i2["graph_steps"] == i1["iters"] - 1
     assert np.array_equal(H(x1), H(x2))
     ref = ctx_for(mesh, smoother=smoother, coarse_mode="kernels", coarse_tol=0.0, coarse_maxit=20)
     x3, i3 = ref.solve(b, tol=1e-9, maxit=200, precond="pmg", prec="fp64", rhs="assembled")
-    assert i3["iters"] == i1["iters"]
+    assert i3["iters"] == i1["iters"] and i3["graph_steps"] == 0
     assert relmax(H(x1), H(x3)) < 1e-9
 
 
