@@ -229,12 +229,9 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
   // element operator constants of this thread's point within its element
   const int lq = threadIdx.x & 7;
   const int i = lq & 1, j = (lq >> 1) & 1, k = lq >> 2;
-  const T d00 = (T)D.a[0], d01 = (T)D.a[1], d10 = (T)D.a[2], d11 = (T)D.a[3];
-  const T di_s = i ? d11 : d00, di_o = i ? d10 : d01;
-  const T dj_s = j ? d11 : d00, dj_o = j ? d10 : d01;
-  const T dk_s = k ? d11 : d00, dk_o = k ? d10 : d01;
-  const T ti_o = i ? d01 : d10, tj_o = j ? d01 : d10, tk_o = k ? d01 : d10;
-  const T h1 = (T)a.h1, h2 = (T)a.h2;
+  // signs of the order-1 derivative at this point's position in its element
+  const T sr_ = i ? T(1) : T(-1), ss_ = j ? T(1) : T(-1), st_ = k ? T(1) : T(-1);
+  const T h1q = (T)(0.25 * a.h1), h2 = (T)a.h2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // node state (slot c: node threadIdx.x + c * PT of the sub-domain)
   T x[NPT], r[NPT], u[NPT], w[NPT], z[NPT], qv[NPT], sv[NPT], p[NPT], di[NPT], mv[NPT];
@@ -285,17 +282,20 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
       else if (ch + 1 < nch) fetch_g(ch + 1, gn);
       const int32_t pn = lv ? s_p2n[bp] : 0;
       const T uu = lv ? s_m[pn & NODE_MASK] : T(0);
-      const T ur = di_s * uu + di_o * __shfl_xor_sync(0xffffffffu, uu, 1);
-      const T us = dj_s * uu + dj_o * __shfl_xor_sync(0xffffffffu, uu, 2);
-      const T ut = dk_s * uu + dk_o * __shfl_xor_sync(0xffffffffu, uu, 4);
+      // order 1: D-hat = [-1/2 1/2; -1/2 1/2], so each derivative is the difference
+      // u(1) - u(0) of the line (times 1/2) and each transposed term the signed sum of
+      // the line's two values (times 1/2); both halves are in h1q = h1 / 4
+      const T ur = sr_ * (uu - __shfl_xor_sync(0xffffffffu, uu, 1));
+      const T us = ss_ * (uu - __shfl_xor_sync(0xffffffffu, uu, 2));
+      const T ut = st_ * (uu - __shfl_xor_sync(0xffffffffu, uu, 4));
       // G11 G12 G13 G22 G23 G33 B (zero past the last point)
-      const T wr = h1 * (gc[0] * ur + gc[1] * us + gc[2] * ut);
-      const T ws = h1 * (gc[1] * ur + gc[3] * us + gc[4] * ut);
-      const T wt = h1 * (gc[2] * ur + gc[4] * us + gc[5] * ut);
-      const T bu = h2 * gc[6] * uu;
-      T wv = bu + di_s * wr + ti_o * __shfl_xor_sync(0xffffffffu, wr, 1);
-      wv += dj_s * ws + tj_o * __shfl_xor_sync(0xffffffffu, ws, 2);
-      wv += dk_s * wt + tk_o * __shfl_xor_sync(0xffffffffu, wt, 4);
+      const T wr = h1q * (gc[0] * ur + gc[1] * us + gc[2] * ut);
+      const T ws = h1q * (gc[1] * ur + gc[3] * us + gc[4] * ut);
+      const T wt = h1q * (gc[2] * ur + gc[4] * us + gc[5] * ut);
+      T wv = h2 * gc[6] * uu;
+      wv += sr_ * (wr + __shfl_xor_sync(0xffffffffu, wr, 1));
+      wv += ss_ * (ws + __shfl_xor_sync(0xffffffffu, ws, 2));
+      wv += st_ * (wt + __shfl_xor_sync(0xffffffffu, wt, 4));
       if (lv) {
         s_pt[bp] = wv;
         if (pn < 0) {
