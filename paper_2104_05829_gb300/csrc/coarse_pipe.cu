@@ -184,7 +184,7 @@ struct SpinBound {
 
 // Every block publishes tagged words and waits only on the words it reads.
 template <typename T, typename GT, int NPT, bool SMEM_G>
-__global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a, Mat64 D) {
+__global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
   using TW = Tagged<T>;
   using W = typename TW::W;
   constexpr int GB = sizeof(T) == 8 ? 4 : 8;   // exchange words in flight per batch
@@ -797,8 +797,7 @@ int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool
   }
   if (occ_per_sm < 1 || L.pp_blocks > occ_per_sm * nsm) return SEM_OK;
   a.G = G;
-  Mat64 D = L.D;
-  void* args[] = {&a, &D};
+  void* args[] = {&a};
   SEM_CUDA_TRY(cudaMemsetAsync(a.err, 0, sizeof(int), s));
   // epochs start at 1, so no stale word of an earlier launch can match
   using W = typename Tagged<T>::W;
