@@ -188,12 +188,13 @@ __device__ __forceinline__ void eo_deriv(const AdvOps<T, NP>& P, const T (&v)[nq
   }
 }
 
-// resident blocks requested from the register allocator: three in FP32 (13.5 warps per
-// SM; two at N = 8, where three spill), two in FP64 (a few hundred bytes of spills,
-// measured 1.26x faster at N = 7 than one block with no spills)
+// resident blocks requested from the register allocator: four in FP32 up to N = 7 (18
+// warps per SM, 96 registers with a 128-byte spill: measured 1.63 ms against 1.74 ms at
+// three blocks with no spill on the 32^3 box), two at N = 8; two in FP64 (a few hundred
+// bytes of spills, measured 1.26x faster at N = 7 than one block with no spills)
 template <typename T, int NP>
 __host__ __device__ constexpr int adv_min_blocks() {
-  return sizeof(T) == 4 ? (NP <= 8 ? 3 : 2) : 2;
+  return sizeof(T) == 4 ? (NP <= 8 ? 4 : 2) : 2;
 }
 
 template <typename T, int NP>
