@@ -95,3 +95,38 @@ def test_projection_entry_points_reject_null_on_host(lib):
     assert lib.sem_proj_update(None, None, 0, None, None, None, None) == L.SEM_EINVAL
     assert lib.sem_solve_proj(None, None, None, None, 1e-8, 10, 0, 0, 0, None, None, None) == L.SEM_EINVAL
     lib.sem_proj_free(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the field offsets and sizes the C compiler
+    gives the header's structures (gcc on this host; no GPU)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2104_05829_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sem_mesh": _lib.SemMesh, "sem_opts": _lib.SemOpts, "sem_coef": _lib.SemCoef,
+               "sem_info": _lib.SemInfo, "sem_level_desc": _lib.SemLevelDesc}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sem.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
