@@ -185,6 +185,14 @@ def build_mesh(e1: int, N: int):
     return mesh
 
 
+def arm_config(elements: int, E: int, nL: int, nG: int, world: int) -> dict:
+    """The workload both arms report (the reference arm times the oracle on the same one)."""
+    return {"workload": f"FP64 Helmholtz Ax+gs (h1=1, h2=0.5) on a {elements}^3-element warped "
+                        f"unit-cube box, N=7, u ~ U[-1,1] continuous (seed 0)",
+            "E": E, "N": 7, "n_L": nL, "n_G": nG, "parallelism": f"replicas x{world}",
+            "l2": f"inputs larger than L2 ({64 * nL / 1e9:.1f} GB read per step vs 129 MB L2)"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -197,7 +205,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"Ax+gs, FP64 Helmholtz (h1=1, h2=0.5), {args.elements}^3 warped box, N=7"},
+            "config": arm_config(args.elements, int(mesh["E"]), int(mesh["x"].size), int(mesh["n_lattice"]), args.gpus),
             "cpu_baseline": {**timed[-1], "value": v},
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -507,10 +515,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32x2" if pairs else "f64", "data": "synthetic",
-            "config": {"workload": f"FP64 Helmholtz Ax+gs (h1=1, h2=0.5) on a {args.elements}^3-element warped "
-                                   f"unit-cube box, N=7, u ~ U[-1,1] continuous (seed 0)",
-                       "E": E, "N": 7, "n_L": nL, "n_G": nG, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (1.1 GB read per step vs 129 MB L2)"},
+            "config": arm_config(args.elements, E, nL, nG, world),
             "roofline": roof, "gpu_launches": 2 * args.steps,
             "clocks": clk.summary()}
 
