@@ -70,11 +70,11 @@ extern "C" {
 #define SEM_SMOOTH_JACOBI 0  /* Chebyshev-accelerated Jacobi (CHEBY-JAC) */
 #define SEM_SMOOTH_ASM 1     /* Chebyshev-accelerated overlapping Schwarz with FDM local solves (CHEBY-ASM) */
 
-/* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in all of them */
-#define SEM_COARSE_AUTO 0     /* the first that applies of PIPE, GRID, CLUSTER, KERNELS */
-#define SEM_COARSE_CLUSTER 1  /* FP32/BF16 V-cycles: one launch on one cluster, problem held on chip; else KERNELS */
-#define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches */
-#define SEM_COARSE_GRID 3     /* one cooperative launch over the whole GPU when it fits; else KERNELS */
+/* execution of the coarse Jacobi-PCG (sem_opts.coarse_mode); the algorithm is the same in both.
+ * Values 1 and 3 are not used (SEM_EINVAL). */
+#define SEM_COARSE_AUTO 0     /* PIPE where it fits, else KERNELS */
+#define SEM_COARSE_KERNELS 2  /* a few kernels per iteration, launched in batches (waits on the host:
+                                 the preconditioner step is then launched directly, not from a graph) */
 #define SEM_COARSE_PIPE 4     /* pipelined PCG on one sub-domain per SM in one cooperative launch; blocks
                                  exchange tagged words, no grid barrier; when it fits, else KERNELS */
 
@@ -93,6 +93,7 @@ extern "C" {
 
 typedef struct sem_ctx sem_ctx;
 typedef struct sem_proj sem_proj;    /* projection space of earlier solutions (sem_proj_create) */
+typedef struct sem_halo sem_halo;    /* interface nodes shared with other ranks (sem_halo_create) */
 #define SEM_PROJ_MAX 16              /* largest basis a projection space may keep */
 
 /* Mesh description (all HOST pointers, copied during sem_setup). */
@@ -120,6 +121,11 @@ typedef struct {
   int32_t prec_copies;       /* SEM_BUILD_* bits: factor copies to build (default: all three) */
   int32_t smoother;          /* SEM_SMOOTH_JACOBI (CHEBY-JAC, default) or SEM_SMOOTH_ASM (CHEBY-ASM) */
   int32_t coarse_mode;       /* how the order-1 coarse Jacobi-PCG runs: SEM_COARSE_* (default AUTO) */
+  int64_t spin_limit;        /* SM clock cycles a device-side wait may spin before it gives up (2^31, about a
+                                second at GB300's clock; >= 0). A wait that gives up makes the solve that
+                                launched it return SEM_EBREAKDOWN (the coarse solve's exchange waits) or turns
+                                the outputs of the waiting block into NaN (the FP32 operator's bulk-copy wait,
+                                which then waits once more, with the default limit, for its copies to land) */
 } sem_opts;
 
 /* Coefficients h1 (diffusion) and h2 (mass) of A = D^T h1 G D + h2 B. */
@@ -345,6 +351,50 @@ int sem_dot(sem_ctx* ctx, const double* a_L, const double* b_L, double* out, voi
  * unique-node product pass the owner mask: 1 where label[l] == l and dmask[l] == 0
  * (sem_get_maps). */
 int sem_dot_static(const double* a, const double* b, const uint8_t* mask, int64_t n, double* out, void* stream);
+
+/* ---- Element partitioning across GPUs and the interface exchange (Section 3.1,
+ * "Domain Partitioning": elements are split among ranks; Section 3.2, "Parallel
+ * Communication": the gather-scatter becomes each rank's own QQ^T plus the exchange
+ * of partial sums at the nodes shared with other ranks, and the elements on the
+ * partition boundary are computed first so that the exchange overlaps the others).
+ * A rank builds a context from its own elements (global ids kept); the sum over
+ * ranks of the halo buffers is the caller's collective (e.g. an all-reduce). ---- */
+
+/* Recursive coordinate bisection of E element centroids (cx, cy, cz: HOST, E each)
+ * into nparts parts of sizes within one of each other: part[e] in 0..nparts-1 (HOST,
+ * caller-allocated). Each bisection splits the longest extent of the part's centroids
+ * at the median (ties by element index). No GPU. Errors: SEM_EINVAL (1 <= nparts <= E). */
+int sem_partition_rcb(int32_t E, const double* cx, const double* cy, const double* cz, int32_t nparts,
+                      int32_t* part);
+/* w_L = A_L u_L on elements e0 .. e1-1 of the fine level only (eq. Ae; other elements'
+ * entries of w_L are not touched). u_L, w_L and coef->h1_L are whole L-vectors. flags 0
+ * (FP64) or SEM_AX_PAIRS (FP32-pair arithmetic, scalar h1). Errors: SEM_EINVAL. */
+int sem_ax_elements(sem_ctx* ctx, int32_t e0, int32_t e1, const double* u_L, double* w_L, const sem_coef* coef,
+                    int flags, void* stream);
+/* Interface of this rank: n global ids (HOST, each held by this context's fine level)
+ * and for each its position pos[i] in an exchange buffer of nbuf doubles (HOST arrays,
+ * copied). Synchronous. Errors: SEM_EINVAL (an id not held here, a position outside
+ * 0..nbuf-1), SEM_ENOMEM, SEM_ECUDA. */
+int sem_halo_create(sem_ctx* ctx, int64_t n, const int64_t* gid, const int64_t* pos, int64_t nbuf,
+                    sem_halo** out);
+void sem_halo_free(sem_halo* halo);
+/* buf (DEVICE, nbuf doubles) <- 0, then buf[pos[i]] = the sum of this rank's local
+ * copies of interface node i in w_L (ascending local index). Asynchronous. */
+int sem_halo_gather(sem_halo* halo, const double* w_L, double* buf, void* stream);
+/* every local copy of interface node i in w_L <- buf[pos[i]] (with SEM_GS_ADD_MASK: 0 at
+ * Dirichlet nodes). With buf the sum over ranks of the gathered buffers and w_L this
+ * rank's own QQ^T of A_L u, this completes the gather-scatter of the whole mesh.
+ * Asynchronous. */
+int sem_halo_scatter(sem_halo* halo, const double* buf, double* w_L, int flags, void* stream);
+
+/* Arithmetic peaks of the current device, measured with plain kernels and CUDA
+ * events on the legacy default stream (the paper has no counterpart; the
+ * library's roofline reports divide by these). out[0]: FP64 FMA, out[1]: FP64
+ * mma.sync (m16n8k8, changing operands), out[2]: FP32 FMA, all in TFLOP/s
+ * (2 flops per multiply-add). Allocates and frees a scratch of 8 blocks x 256
+ * doubles per SM; takes about 0.1 s. Synchronous. Errors: SEM_EINVAL (NULL),
+ * SEM_ENOMEM, SEM_ECUDA. */
+int sem_measure_peaks(double* out);
 
 /* ---- read-back of setup products, for validation (HOST outputs, synchronous) ---- */
 /* Canonical gather-scatter maps of `level` (any pointer may be NULL):

@@ -5,6 +5,6 @@ script and a thin Python binding. Nothing here falls back to the CPU: if the
 library is not built, every call raises.
 """
 from ._lib import SemError, load  # noqa: F401
-from .sem import Projection, SemContext, default_opts, gll  # noqa: F401
+from .sem import Projection, SemContext, default_opts, gll, measure_peaks  # noqa: F401
 
-__all__ = ["Projection", "SemContext", "SemError", "default_opts", "gll", "load"]
+__all__ = ["Projection", "SemContext", "SemError", "default_opts", "gll", "load", "measure_peaks"]

@@ -27,7 +27,7 @@ SEM_BUILD_FP32, SEM_BUILD_BF16G, SEM_BUILD_PAIRS = 1, 2, 4
 SEM_GRAD_SUM = 1
 SEM_SMOOTH_JACOBI, SEM_SMOOTH_ASM = 0, 1
 SEM_ADV_LOCAL, SEM_ADV_ASSEMBLE = 0, 1
-SEM_COARSE_AUTO, SEM_COARSE_CLUSTER, SEM_COARSE_KERNELS, SEM_COARSE_GRID, SEM_COARSE_PIPE = 0, 1, 2, 3, 4
+SEM_COARSE_AUTO, SEM_COARSE_KERNELS, SEM_COARSE_PIPE = 0, 2, 4
 
 
 class SemMesh(C.Structure):
@@ -42,7 +42,7 @@ class SemOpts(C.Structure):
                 ("cheb_lmax_factor", C.c_double), ("lanczos_steps", C.c_int32),
                 ("lanczos_seed", C.c_uint64), ("coarse_tol", C.c_double),
                 ("coarse_maxit", C.c_int32), ("prec_copies", C.c_int32), ("smoother", C.c_int32),
-                ("coarse_mode", C.c_int32)]
+                ("coarse_mode", C.c_int32), ("spin_limit", C.c_int64)]
 
 
 class SemCoef(C.Structure):
@@ -103,6 +103,13 @@ SIGNATURES = {
     "sem_mass_local": (_I, [_P, _P, _P, _P]),
     "sem_dot": (_I, [_P, _P, _P, _P, _P]),
     "sem_dot_static": (_I, [_P, _P, _P, C.c_int64, _P, _P]),
+    "sem_measure_peaks": (_I, [_P]),
+    "sem_partition_rcb": (_I, [C.c_int32, _P, _P, _P, C.c_int32, _P]),
+    "sem_ax_elements": (_I, [_P, C.c_int32, C.c_int32, _P, _P, C.POINTER(SemCoef), _I, _P]),
+    "sem_halo_create": (_I, [_P, C.c_int64, _P, _P, C.c_int64, C.POINTER(_P)]),
+    "sem_halo_free": (None, [_P]),
+    "sem_halo_gather": (_I, [_P, _P, _P, _P]),
+    "sem_halo_scatter": (_I, [_P, _P, _P, _I, _P]),
     "sem_get_maps": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "sem_get_geom": (_I, [_P, _I, _P]),
     "sem_get_geom_lowp": (_I, [_P, _I, _I, _P]),

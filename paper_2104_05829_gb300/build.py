@@ -18,8 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsem.so")
-SOURCES = ["setup.cu", "gsmap.cu", "ax.cu", "ax_eo.cu", "gs.cu", "blas.cu", "solve.cu", "coarse.cu", "dot_static.cu",
-           "proj.cu", "asm.cu", "coarse_grid.cu", "coarse_pipe.cu", "advect.cu"]
+SOURCES = ["setup.cu", "gsmap.cu", "ax.cu", "ax_eo.cu", "gs.cu", "blas.cu", "solve.cu", "dot_static.cu",
+           "proj.cu", "asm.cu", "coarse_pipe.cu", "advect.cu", "peaks.cu", "dist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

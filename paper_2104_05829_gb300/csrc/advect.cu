@@ -425,11 +425,8 @@ int advect_launch(const Level& L, const AdvData& A, const T* c, const T* u, T* w
       P.mr[r] = (T)d(H, r);
     }
   constexpr size_t smem = advect_smem<T, NP>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_advect<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+  static PerDevice<bool> attr;
+  SEM_TRY(smem_attr_once(attr, (const void*)k_advect<T, NP>, smem));
   k_advect<T, NP><<<L.E, AdvShape<NP>::T, smem, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w, P);
   SEM_LAUNCH_CHECK();
   return SEM_OK;

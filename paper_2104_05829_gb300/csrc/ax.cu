@@ -181,7 +181,7 @@ __host__ __device__ constexpr size_t bulk_smem() {
 template <typename GT, int NP, bool VARH1>
 __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
     k_ax_bulk(int E, const float* __restrict__ u, float* __restrict__ w, const GT* __restrict__ G, Mat32 Dm,
-              float h1, float h2, const double* __restrict__ h1L, const double* skip) {
+              float h1, float h2, const double* __restrict__ h1L, const double* skip, long long spin) {
   using T = float;
   constexpr int EPB = bulk_epb<NP>();
   constexpr int NP2 = NP * NP, NP3 = NP * NP * NP, GE = 7 * NP3;
@@ -221,10 +221,14 @@ __global__ void __launch_bounds__(NP* NP* bulk_epb<NP>())
   T ru[NP];
   const size_t ebase = (size_t)e * NP3;
   __syncthreads();   // s_D and the barrier's initialisation are visible
-  if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
+  if (!__syncthreads_and(mbar_wait(&bar, 0, spin) ? 1 : 0)) {
     if (active)
 #pragma unroll
       for (int k = 0; k < NP; ++k) w[ebase + k * NP2 + ij] = __int_as_float(0x7fc00000);
+    // the copies may still be in flight into this block's shared memory: wait for
+    // them once more (bounded again) before the block releases it
+    if (tid == 0) mbar_wait(&bar, 0);
+    __syncthreads();
     return;
   }
 #pragma unroll
@@ -273,19 +277,16 @@ int launch_ax_bulk(const Level& L, const float* u, float* w, const GT* G, const 
                    const double* h1L, const double* skip, cudaStream_t s) {
   constexpr int EPB = bulk_epb<NP>();
   constexpr size_t smem = bulk_smem<GT, NP>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_ax_bulk<GT, NP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_ax_bulk<GT, NP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    attr = true;
-  }
+  static PerDevice<bool> attr[2];
+  SEM_TRY(smem_attr_once(attr[0], (const void*)k_ax_bulk<GT, NP, false>, smem));
+  SEM_TRY(smem_attr_once(attr[1], (const void*)k_ax_bulk<GT, NP, true>, smem));
   dim3 grid((L.E + EPB - 1) / EPB), block(NP * NP * EPB);
   if (h1L)
-    k_ax_bulk<GT, NP, true><<<grid, block, smem, s>>>(L.E, u, w, G, Dm, (float)h1, (float)h2, h1L, skip);
+    k_ax_bulk<GT, NP, true><<<grid, block, smem, s>>>(L.E, u, w, G, Dm, (float)h1, (float)h2, h1L, skip,
+                                                      L.spin_limit);
   else
-    k_ax_bulk<GT, NP, false><<<grid, block, smem, s>>>(L.E, u, w, G, Dm, (float)h1, (float)h2, nullptr, skip);
+    k_ax_bulk<GT, NP, false><<<grid, block, smem, s>>>(L.E, u, w, G, Dm, (float)h1, (float)h2, nullptr, skip,
+                                                       L.spin_limit);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
@@ -294,13 +295,18 @@ template <int NP>
 int ax_dispatch_np(const Level& L, int prec, const void* u, void* w, double h1, double h2, const double* h1L,
                    const double* skip, cudaStream_t s) {
   if (prec == SEM_FP64) return ax_eo_apply(L, (const double*)u, (double*)w, h1, h2, h1L, skip, s);
+  // the bulk copy of u needs a 16-byte aligned source (the per-element sizes are
+  // multiples of 16 bytes and the factors are library allocations), so a caller's
+  // vector that starts elsewhere, e.g. an offset view, takes the plain-load kernel
+  const bool u16 = ((uintptr_t)u & 15u) == 0;
   if (prec == SEM_FP32) {
     if constexpr (bulk_ok<float, NP>())
-      return launch_ax_bulk<float, NP>(L, (const float*)u, (float*)w, L.G32, L.Df, h1, h2, h1L, skip, s);
+      if (u16) return launch_ax_bulk<float, NP>(L, (const float*)u, (float*)w, L.G32, L.Df, h1, h2, h1L, skip, s);
     return launch_ax<float, float, NP>(L, (const float*)u, (float*)w, L.G32, L.Df, h1, h2, h1L, skip, s);
   }
   if constexpr (bulk_ok<__nv_bfloat16, NP>())
-    return launch_ax_bulk<__nv_bfloat16, NP>(L, (const float*)u, (float*)w, L.G16, L.Df, h1, h2, h1L, skip, s);
+    if (u16)
+      return launch_ax_bulk<__nv_bfloat16, NP>(L, (const float*)u, (float*)w, L.G16, L.Df, h1, h2, h1L, skip, s);
   return launch_ax<float, __nv_bfloat16, NP>(L, (const float*)u, (float*)w, L.G16, L.Df, h1, h2, h1L, skip, s);
 }
 

@@ -310,6 +310,25 @@ int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double
   return eo_launch<ArPair>(L, u, w, L.G2, h1, h2, nullptr, nullptr, s);
 }
 
+// The element operator on elements [e0, e1) only (FP64, or FP32 pairs with a scalar h1):
+// the same kernels on a view of the level whose pointers start at element e0.
+int ax_eo_apply_range(const Level& L, int e0, int e1, const double* u, double* w, double h1, double h2,
+                      const double* h1L, bool pairs, cudaStream_t s) {
+  if (e1 <= e0) return SEM_OK;
+  const size_t off = (size_t)e0 * L.NP * L.NP * L.NP;
+  Level V = L;
+  V.E = e1 - e0;
+  V.nL = (int64_t)V.E * L.NP * L.NP * L.NP;
+  if (pairs) {
+    if (!L.G2 || h1L) {
+      set_detail("FP32-pair factors not built, or nodal h1 with pairs");
+      return SEM_EINVAL;
+    }
+    return eo_launch<ArPair>(V, u + off, w + off, L.G2 + 7 * off, h1, h2, nullptr, nullptr, s);
+  }
+  return eo_launch<ArF64>(V, u + off, w + off, L.G + 7 * off, h1, h2, h1L ? h1L + off : nullptr, nullptr, s);
+}
+
 // (hi, lo) FP32 split of the FP64 factors for the pair kernel.
 int pairs_build(Level& L, cudaStream_t s) {
   if (!L.G2) {

@@ -27,19 +27,30 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-// true once phase `parity` of the barrier has completed; false after about a
-// second of SM clock (2^31 cycles)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// true once phase `parity` of the barrier has completed; false after `limit` SM
+// clock cycles (2^31 by default: about a second). try_wait may suspend the thread
+// for a while before it reports an incomplete phase, which suits long limits; a
+// short limit (below 2^20 cycles) polls with the non-blocking test_wait instead, so
+// that the limit is what ends the wait.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = 1ll << 31) {
   const long long t0 = clock64();
+  const bool poll = limit < (1ll << 20);
   while (true) {
     uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
+    if (poll)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 

@@ -81,6 +81,8 @@ struct PipeArgs {
   double* part;                     // [2][3][B] tagged partials
   int* err;
   double* sc;                       // outputs: S_ITER, S_TOTAL, S_RR, S_BB, S_DONE, S_BREAK
+  double* outer_sc;                 // the calling solve's scalars: S_BREAK and S_DONE set when a wait gave up
+  long long spin;                   // SM clocks a wait may spin
 };
 
 __host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
@@ -157,24 +159,25 @@ struct Tagged<double> {
   __device__ static double val(const W& w) { return __hiloint2double((int)(unsigned)w.hi, (int)(unsigned)w.lo); }
 };
 
-// Bound of a wait on tagged words: go() is false once the wait has run about a
-// second of SM clock (then the global and block error flags are set) or another
-// block has given up.
+// Bound of a wait on tagged words: go() is false once the wait has run `limit` SM
+// clock cycles (then the global and block error flags are set; the default is about
+// a second) or, looked at every 16 polls, another block has given up.
 struct SpinBound {
-  long long t0;
+  long long t0, limit;
   unsigned polls;
-  __device__ SpinBound() {
+  __device__ explicit SpinBound(long long lim) {
     t0 = clock64();
+    limit = lim;
     polls = 0;
   }
   __device__ bool go(int* err, volatile int* s_err) {
-    if ((++polls & 15u) != 0) return true;
-    if (*s_err != 0 || *(volatile int*)err != 0) {
+    if (clock64() - t0 > limit) {
+      atomicExch(err, 1);
       *s_err = 1;
       return false;
     }
-    if (clock64() - t0 > (1ll << 31)) {
-      atomicExch(err, 1);
+    if ((++polls & 15u) != 0) return true;
+    if (*s_err != 0 || *(volatile int*)err != 0) {
       *s_err = 1;
       return false;
     }
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
 #pragma unroll
         for (int t = 0; t < GB; ++t)
           if ((need >> t) & 1u) wd[t] = TW::ld(xtag + base + lr[t]);
-        SpinBound sb;
+        SpinBound sb(a.spin);
         while (true) {
 #pragma unroll
           for (int t = 0; t < GB; ++t)
@@ -374,7 +377,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
       } else {
         const W* wp = xtag + base + (-(int64_t)e - 1);
         W wd = TW::ld(wp);
-        SpinBound sb;
+        SpinBound sb(a.spin);
         while (!TW::ok(wd, ep) && sb.go(a.err, &s_err)) wd = TW::ld(wp);
         vt = TW::val(wd);
       }
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
             }
           }
         }
-        SpinBound sb;
+        SpinBound sb(a.spin);
         while (true) {
 #pragma unroll
           for (int kk = 0; kk < GB; ++kk)
@@ -550,6 +553,12 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
   T* xg = static_cast<T*>(a.x);
   for (int bp = threadIdx.x; bp < npt; bp += PT)
     xg[(int64_t)s_el[bp >> 3] * NPC3 + (bp & 7)] = s_m[s_p2n[bp] & NODE_MASK];
+  // a block whose wait gave up holds stale values: the calling solve must stop with a
+  // breakdown, whichever block saw it (every such block writes the same flags)
+  if (threadIdx.x == 0 && (s_err != 0 || *(volatile int*)a.err != 0) && a.outer_sc) {
+    a.outer_sc[S_BREAK] = 1;
+    a.outer_sc[S_DONE] = 1;
+  }
   if (bk == 0 && threadIdx.x == 32 * (PW - 3)) {
     a.sc[S_ITER] = it;
     a.sc[S_TOTAL] += it;
@@ -559,6 +568,20 @@ __global__ void __launch_bounds__(PT, 1) k_coarse_pipe(PipeArgs a) {
     a.sc[S_DONE] = 1;
   }
 }
+
+template <typename V>
+int upload(V** dst, const std::vector<V>& src, cudaStream_t s) {
+  if (cudaMalloc((void**)dst, src.size() * sizeof(V) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    set_detail("cudaMalloc failed (sub-domain coarse solve)");
+    return SEM_ENOMEM;
+  }
+  if (!src.empty()) SEM_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, s));
+  return SEM_OK;
+}
+
+}  // namespace
 
 // Recursive coordinate bisection: el[0..n) goes to parts part0 .. part0 + parts - 1,
 // part sizes within one of each other; each part's elements end up ascending.
@@ -586,20 +609,6 @@ void rcb(int32_t* el, int n, int parts, int part0, int32_t base, const std::vect
   rcb(el, n1, p1, part0, base, c, el_off);
   rcb(el + n1, n - n1, parts - p1, part0 + p1, base + n1, c, el_off);
 }
-
-template <typename V>
-int upload(V** dst, const std::vector<V>& src, cudaStream_t s) {
-  if (cudaMalloc((void**)dst, src.size() * sizeof(V) + 16) != cudaSuccess) {
-    cudaGetLastError();
-    *dst = nullptr;
-    set_detail("cudaMalloc failed (sub-domain coarse solve)");
-    return SEM_ENOMEM;
-  }
-  if (!src.empty()) SEM_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, s));
-  return SEM_OK;
-}
-
-}  // namespace
 
 namespace {
 
@@ -775,25 +784,37 @@ int try_launch(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, bool
   const size_t smem = PipeSmem::make<T, GT, SMEM_G>(a.max_el, a.max_nd, a.max_cp).total;
   if (smem > 220 * 1024) return SEM_OK;
   const void* f = (const void*)k_coarse_pipe<T, GT, NPT, SMEM_G>;
-  // the shared-memory attribute and the occupancy are asked once per size, so that a
-  // launch captured into a CUDA graph issues no such calls
-  static size_t attr_smem = 48 * 1024, occ_smem = 0;
-  static int occ_per_sm = 0;
-  if (smem > attr_smem) {
-    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      return SEM_OK;
+  // the shared-memory attribute and the occupancy are asked once per size and device,
+  // so that a launch captured into a CUDA graph issues no such calls
+  struct Occ {
+    size_t attr_smem, occ_smem;
+    int per_sm;
+  };
+  static PerDevice<Occ> cache;
+  int dev = 0;
+  SEM_TRY(current_device(&dev));
+  int occ_per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(cache.m);
+    Occ& o = cache.v[dev];
+    if (o.attr_smem < 48 * 1024) o.attr_smem = 48 * 1024;
+    if (smem > o.attr_smem) {
+      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return SEM_OK;
+      }
+      o.attr_smem = smem;
     }
-    attr_smem = smem;
-  }
-  if (occ_smem != smem) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, PT, smem) != cudaSuccess) {
-      cudaGetLastError();
-      return SEM_OK;
+    if (o.occ_smem != smem) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, PT, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return SEM_OK;
+      }
+      o.occ_smem = smem;
+      o.per_sm = per_sm;
     }
-    occ_smem = smem;
-    occ_per_sm = per_sm;
+    occ_per_sm = o.per_sm;
   }
   if (occ_per_sm < 1 || L.pp_blocks > occ_per_sm * nsm) return SEM_OK;
   a.G = G;
@@ -829,7 +850,7 @@ int launch_pipe(Level& L, const GT* G, PipeArgs& a, int nsm, cudaStream_t s, boo
 // Pipelined sub-domain coarse solve at order 1 (FP64, FP32 or BF16-factor V-cycles);
 // *used = false when it does not apply. err: [1].
 int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
-                      double tol, int maxit, double* sc, int* err, cudaStream_t s, bool* used) {
+                      double tol, int maxit, double* sc, int* err, double* outer_sc, cudaStream_t s, bool* used) {
   *used = false;
   if (L.NP != NPC) return SEM_OK;
   SEM_TRY(coarse_pipe_build(L, s));
@@ -859,6 +880,8 @@ int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* di
   a.part = L.pp_part;
   a.err = err;
   a.sc = sc;
+  a.outer_sc = outer_sc;
+  a.spin = L.spin_limit;
   if (prec == SEM_FP64) return launch_pipe<double, double>(L, L.G, a, nsm, s, used);
   if (prec == SEM_FP32) return launch_pipe<float, float>(L, L.G32, a, nsm, s, used);
   return launch_pipe<float, __nv_bfloat16>(L, L.G16, a, nsm, s, used);

@@ -33,8 +33,7 @@ struct DotScratch {
 static __device__ __align__(256) DotScratch g_dot_scratch;
 
 std::mutex g_addr_mutex;
-constexpr int MAX_DEVICES = 64;
-DotScratch* g_addr[MAX_DEVICES] = {};
+DotScratch* g_addr[sem::MAX_DEVICES] = {};
 
 __global__ void __launch_bounds__(DS_THREADS)
     k_dot_static(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
@@ -79,7 +78,7 @@ __global__ void __launch_bounds__(DS_THREADS)
 int scratch_address(DotScratch** out) {
   int dev = -1;
   SEM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAX_DEVICES) {
+  if (dev < 0 || dev >= sem::MAX_DEVICES) {
     sem::set_detail("sem_dot_static: device ordinal %d out of range", dev);
     return SEM_EINVAL;
   }

@@ -6,7 +6,9 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "sem.h"
 
@@ -56,6 +58,7 @@ void host_interp(int nc, const double* xi_from, int nt, const double* x_to, doub
 
 struct Level {
   int N = 0, NP = 0, E = 0;
+  long long spin_limit = 1ll << 31;   // SM clocks a device-side wait of this level's kernels may spin
   int64_t nL = 0, nG = 0, n_ids = 0, n_idx = 0, n_seg = 0, n_seg_idx = 0;
   Mat64 D{};                 // D_hat of this order
   Mat32 Df{};
@@ -112,9 +115,6 @@ struct Level {
   int32_t* sch_poff = nullptr;    // CSR offsets into sch_psrc
   int32_t* sch_psrc = nullptr;    // staged slots per point, in slot order
   int64_t sch_npts = 0;
-  // on-chip cluster coarse solve: (CTA rank << 24 | offset) of every gather-scatter copy
-  int32_t* cl_loc = nullptr;      // [n_seg_idx]
-  int cl_loc_epc = 0;             // elements per CTA the locations were computed for
   // sub-domain coarse solve (coarse_pipe.cu; built on first use at order 1)
   int pp_blocks = 0;              // sub-domains, one block each; 0 not built, -1 does not apply
   int pp_max_el = 0, pp_max_nd = 0, pp_max_cp = 0;   // largest sub-domain: elements, nodes, copy entries
@@ -196,9 +196,7 @@ struct Ctx {
   uint64_t pc_gen = 0;                       // bumped by every preconditioner set-up
   bool pc_graph_off = false;                 // a capture failed: direct launches from then on
   int graph_steps = 0;                       // graph replays in the current solve
-  // scratch of the whole-GPU coarse solve
-  double* cg_part = nullptr;                 // [3 * COARSE_GRID_MAX]
-  unsigned* cg_bar = nullptr;                // [COARSE_GRID_MAX + 1]
+  // error flag of the one-launch coarse solve (set when a bounded wait gives up)
   int* cg_err = nullptr;                     // [1]
 };
 
@@ -218,25 +216,25 @@ int geom_compute(Level& L, int* d_bad, cudaStream_t s);
 int ax_eo_apply(const Level& L, const double* u, double* w, double h1, double h2, const double* h1L,
                 const double* skip, cudaStream_t s);
 
+// elements [e0, e1) of the level only (u, w, h1L: whole-level L-vectors)
+int ax_eo_apply_range(const Level& L, int e0, int e1, const double* u, double* w, double h1, double h2,
+                      const double* h1L, bool pairs, cudaStream_t s);
+
 // ---- ax_eo.cu (FP32-pair variant)
 int pairs_build(Level& L, cudaStream_t s);
 int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s);
 
-// ---- coarse.cu: one-launch coarse Jacobi-PCG on a thread-block cluster
-int coarse_cluster_solve(const Level& L, int prec, const void* b, void* x, void* r, void* p, void* w,
-                         const void* dinv, double h1, double h2, double tol, int maxit, double* sc,
-                         cudaStream_t s, bool* used);
-
-// ---- coarse_grid.cu: one-launch coarse Jacobi-PCG over the whole GPU (cooperative launch)
-constexpr int COARSE_GRID_MAX = 2048;   // largest grid; scratch: part[3 * COARSE_GRID_MAX], bar[COARSE_GRID_MAX + 1], err[1]
-int coarse_grid_solve(const Level& L, int prec, const void* b, void* x, void* p, void* w, const void* dinv,
-                      double h1, double h2, double tol, int maxit, double* sc, double* part, unsigned* bar, int* err,
-                      cudaStream_t s, bool* used);
+// ---- coarse_pipe.cu: recursive coordinate bisection (host): el[0..n) goes to parts
+// part0 .. part0 + parts - 1 (el_off[part] = first position), sizes within one of each
+// other, each part's elements ascending; c[3][E] are the element centroids
+void rcb(int32_t* el, int n, int parts, int part0, int32_t base, const std::vector<double>* c,
+         std::vector<int32_t>& el_off);
 
 // ---- coarse_pipe.cu: one-launch pipelined coarse Jacobi-PCG on sub-domains (cooperative launch)
 int coarse_pipe_build(Level& L, cudaStream_t s);
+// outer_sc: the calling solve's scalar slots (S_BREAK and S_DONE are set there when a wait gives up)
 int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* dinv, double h1, double h2,
-                      double tol, int maxit, double* sc, int* err, cudaStream_t s, bool* used);
+                      double tol, int maxit, double* sc, int* err, double* outer_sc, cudaStream_t s, bool* used);
 
 // ---- gs.cu
 int gs_apply(const Level& L, int prec, void* w, bool mask, cudaStream_t s);
@@ -316,5 +314,36 @@ int restrict_residual(const Level& F, const Level& Cl, int prec, const void* bf,
 
 // helpers
 inline size_t prec_size(int prec) { return prec == SEM_FP64 ? 8 : 4; }
+
+// Launch set-up that is done once per device and remembered (a kernel's shared-
+// memory attribute, an occupancy query), so that launches later captured into a
+// CUDA graph issue no such calls. Each device keeps its own entry, filled under a
+// lock: a second device, or another host thread, does its own set-up.
+constexpr int MAX_DEVICES = 64;
+template <typename V>
+struct PerDevice {
+  std::mutex m;
+  V v[MAX_DEVICES] = {};
+};
+inline int current_device(int* dev) {
+  SEM_CUDA_TRY(cudaGetDevice(dev));
+  if (*dev < 0 || *dev >= MAX_DEVICES) {
+    set_detail("device ordinal %d out of range", *dev);
+    return SEM_EINVAL;
+  }
+  return SEM_OK;
+}
+// Set the dynamic shared-memory limit of kernel f to `bytes` on the current device,
+// once per device.
+inline int smem_attr_once(PerDevice<bool>& cache, const void* f, size_t bytes) {
+  int dev = 0;
+  SEM_TRY(current_device(&dev));
+  std::lock_guard<std::mutex> lock(cache.m);
+  if (!cache.v[dev]) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cache.v[dev] = true;
+  }
+  return SEM_OK;
+}
 
 }  // namespace sem

@@ -223,7 +223,7 @@ void free_level(Level& L) {
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
-                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.cl_loc, L.pp_el_off, L.pp_el,
+                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.pp_el_off, L.pp_el,
                   L.pp_p2n, L.pp_nd_off, L.pp_nd_src, L.pp_nd_fl, L.pp_cp_off, L.pp_cp, L.pp_xbuf, L.pp_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -351,6 +351,7 @@ void sem_default_opts(sem_opts* o) {
   o->prec_copies = SEM_BUILD_FP32 | SEM_BUILD_BF16G | SEM_BUILD_PAIRS;
   o->smoother = SEM_SMOOTH_JACOBI;
   o->coarse_mode = SEM_COARSE_AUTO;
+  o->spin_limit = 1ll << 31;
 }
 
 const char* sem_strerror(int code) {
@@ -374,7 +375,7 @@ void sem_free(sem_ctx* h) {
   for (int l = 0; l < SEM_MAX_LEVELS; ++l) free_level(C->lev[l]);
   advect_free(C->adv);
   void* ptrs[] = {C->red_part, C->red_ticket, C->scal, C->r, C->z, C->p, C->w, C->t,
-                  C->cg_part, C->cg_bar, C->cg_err};
+                  C->cg_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (C->h_scal) cudaFreeHost(C->h_scal);
@@ -413,9 +414,10 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
   sem_opts o;
   if (opts_in) o = *opts_in;
   else sem_default_opts(&o);
-  if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
-      (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM) || o.coarse_mode < SEM_COARSE_AUTO ||
-      o.coarse_mode > SEM_COARSE_PIPE) {
+  if (o.cheb_degree < 1 || o.lanczos_steps < 1 || o.coarse_maxit < 0 || o.spin_limit < 0 ||
+      !(o.cheb_lmax_factor > o.cheb_lmin_factor) ||
+      (o.smoother != SEM_SMOOTH_JACOBI && o.smoother != SEM_SMOOTH_ASM) ||
+      (o.coarse_mode != SEM_COARSE_AUTO && o.coarse_mode != SEM_COARSE_KERNELS && o.coarse_mode != SEM_COARSE_PIPE)) {
     set_detail("invalid smoother / Lanczos / coarse-solve options");
     return SEM_EINVAL;
   }
@@ -487,11 +489,10 @@ int sem_setup(const sem_mesh* m, const sem_opts* opts_in, sem_ctx** out) {
     }
     C->nlevels = (int)l + 1;
   }
+  for (int l = 0; l < C->nlevels; ++l) C->lev[l].spin_limit = o.spin_limit;
   // reduction scratch and fine-level solver workspace
   STEP(dmalloc(&C->red_part, RED_BLOCKS * 4));
   STEP(dmalloc(&C->red_ticket, 1));
-  STEP(dmalloc(&C->cg_part, 3 * COARSE_GRID_MAX));
-  STEP(dmalloc(&C->cg_bar, COARSE_GRID_MAX + 1));
   STEP(dmalloc(&C->cg_err, 1));
   CUSTEP(cudaMemsetAsync(C->red_ticket, 0, sizeof(unsigned), s));
   STEP(dmalloc(&C->scal, 4 * S_NSLOTS));

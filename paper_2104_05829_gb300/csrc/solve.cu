@@ -235,22 +235,13 @@ int coarse_solve(Ctx& C, int l, int prec, const void* b, void* x, cudaStream_t s
   Level& L = C.lev[l];
   VecSet v = vecs(L, prec);
   double* sc = C.scal + 1 * S_NSLOTS;
-  // order 1: the whole solve in one cooperative launch over the whole GPU
-  // (pipelined on sub-domains, or per point), or in one launch on one
-  // thread-block cluster with the problem on chip (FP32 / BF16-factor V-cycles)
+  // order 1: the whole solve in one cooperative launch, pipelined on one
+  // sub-domain per SM, when the sub-domains fit; else the batched kernels below
   bool used = false;
   const int mode = C.opts.coarse_mode;
   if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_PIPE)
     SEM_TRY(coarse_pipe_solve(L, prec, b, x, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol, C.opts.coarse_maxit, sc,
-                              C.cg_err, s, &used));
-  if (used) return SEM_OK;
-  if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_GRID)
-    SEM_TRY(coarse_grid_solve(L, prec, b, x, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
-                              C.opts.coarse_maxit, sc, C.cg_part, C.cg_bar, C.cg_err, s, &used));
-  if (used) return SEM_OK;
-  if (mode == SEM_COARSE_AUTO || mode == SEM_COARSE_CLUSTER)
-    SEM_TRY(coarse_cluster_solve(L, prec, b, x, v.r, v.p, v.w, v.dinv, C.pc_h1, C.pc_h2, C.opts.coarse_tol,
-                                 C.opts.coarse_maxit, sc, s, &used));
+                              C.cg_err, C.scal, s, &used));
   if (used) return SEM_OK;
   SEM_TRY(pcg_begin_tol(C, L, prec, b, nullptr, x, v.r, v.dinv, v.p, sc, C.opts.coarse_tol, s));
   // Iterations go out in batches. After each batch the device's "done" flag is

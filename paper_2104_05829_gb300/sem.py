@@ -51,8 +51,7 @@ def default_opts(**kw) -> L.SemOpts:
         elif k == "smoother":
             o.smoother = {"jacobi": L.SEM_SMOOTH_JACOBI, "asm": L.SEM_SMOOTH_ASM}.get(v, v)
         elif k == "coarse_mode":
-            o.coarse_mode = {"auto": L.SEM_COARSE_AUTO, "cluster": L.SEM_COARSE_CLUSTER,
-                             "kernels": L.SEM_COARSE_KERNELS, "grid": L.SEM_COARSE_GRID,
+            o.coarse_mode = {"auto": L.SEM_COARSE_AUTO, "kernels": L.SEM_COARSE_KERNELS,
                              "pipe": L.SEM_COARSE_PIPE}.get(v, v)
         elif not hasattr(o, k):
             raise KeyError(k)
@@ -132,6 +131,15 @@ class SemContext:
         flags = (L.SEM_AX_ASSEMBLE if assemble else L.SEM_AX_LOCAL) | (L.SEM_AX_PAIRS if pairs else 0)
         L.check(self._lib.sem_ax(self._h, _dev(u, torch.float64, n, "u"), _dev(w, torch.float64, n, "w"),
                                  C.byref(c), flags, _stream(stream)), "sem_ax")
+        return w
+
+    def ax_elements(self, e0, e1, u, w, h1=1.0, h2=0.0, h1_L=None, pairs=False, stream=None):
+        """w_L = A_L u_L on elements e0 .. e1-1 only (sem_ax_elements); other entries untouched."""
+        n = self.nL
+        c = L.SemCoef(float(h1), float(h2), _dev(h1_L, torch.float64, n, "h1_L") if h1_L is not None else None)
+        L.check(self._lib.sem_ax_elements(self._h, int(e0), int(e1), _dev(u, torch.float64, n, "u"),
+                                          _dev(w, torch.float64, n, "w"), C.byref(c),
+                                          L.SEM_AX_PAIRS if pairs else 0, _stream(stream)), "sem_ax_elements")
         return w
 
     def gs(self, w, mask=False, stream=None):
@@ -379,6 +387,63 @@ class Projection:
         return bool(added.value)
 
 
+class Halo:
+    """Interface nodes of this rank (sem_halo_*): gather its partial sums into an exchange
+    buffer at given positions, and write completed sums back to every local copy."""
+
+    def __init__(self, ctx: SemContext, gid, pos, nbuf: int):
+        self._lib = L.load()
+        self.ctx = ctx
+        gid = _host(gid, np.int64)
+        pos = _host(pos, np.int64)
+        if gid.size != pos.size:
+            raise ValueError("gid and pos must have the same length")
+        h = C.c_void_p()
+        L.check(self._lib.sem_halo_create(ctx._h, gid.size, gid.ctypes.data if gid.size else None,
+                                          pos.ctypes.data if pos.size else None, int(nbuf), C.byref(h)),
+                "sem_halo_create")
+        self._h = h
+        self.n, self.nbuf = int(gid.size), int(nbuf)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sem_halo_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _buf(self, buf):
+        if buf.numel() < self.nbuf:
+            raise ValueError(f"the exchange buffer needs {self.nbuf} values")
+        return _dev(buf, torch.float64, buf.numel(), "buf")
+
+    def gather(self, w, buf, stream=None):
+        L.check(self._lib.sem_halo_gather(self._h, _dev(w, torch.float64, self.ctx.nL, "w"), self._buf(buf),
+                                          _stream(stream)), "sem_halo_gather")
+        return buf
+
+    def scatter(self, buf, w, mask=True, stream=None):
+        L.check(self._lib.sem_halo_scatter(self._h, self._buf(buf),
+                                           _dev(w, torch.float64, self.ctx.nL, "w"),
+                                           L.SEM_GS_ADD_MASK if mask else L.SEM_GS_ADD, _stream(stream)),
+                "sem_halo_scatter")
+        return w
+
+
+def partition_rcb(cx, cy, cz, nparts: int) -> np.ndarray:
+    """Recursive coordinate bisection of element centroids into nparts parts (sem_partition_rcb)."""
+    lib = L.load()
+    cx, cy, cz = (np.ascontiguousarray(v, dtype=np.float64).ravel() for v in (cx, cy, cz))
+    part = np.empty(cx.size, np.int32)
+    L.check(lib.sem_partition_rcb(cx.size, cx.ctypes.data, cy.ctypes.data, cz.ctypes.data, int(nparts),
+                                  part.ctypes.data), "sem_partition_rcb")
+    return part
+
+
 class _DeviceView:
     """View of n doubles at a library-owned device address (CUDA array interface); callers
     only copy from it (torch does not accept the interface's read-only flag)."""
@@ -386,6 +451,14 @@ class _DeviceView:
     def __init__(self, ptr: int, n: int):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 2,
                                          "strides": None}
+
+
+def measure_peaks() -> dict:
+    """Measured arithmetic peaks of the current device in TFLOP/s (sem_measure_peaks)."""
+    lib = L.load()
+    out = (C.c_double * 3)()
+    L.check(lib.sem_measure_peaks(out), "sem_measure_peaks")
+    return {"fp64_fma": out[0], "fp64_mma": out[1], "fp32_fma": out[2]}
 
 
 def gll(N: int):

@@ -86,6 +86,26 @@ def test_ax_low_precision(prec, tol):
     assert relmax(w, ref) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("bf16g", 2e-2)])
+def test_ax_low_precision_on_an_offset_view(prec, tol):
+    """A caller's FP32 vector that does not start on a 16-byte boundary (a view at offset 1
+    of a larger tensor) cannot be staged by the bulk copy; the operator then reads it with
+    plain loads and gives the same result."""
+    dev()
+    mesh, ctx, lev = _setup((4, 3, 3), 7)
+    u = si.uniform_field(mesh, 0)
+    n = u.size
+    big = torch.zeros(n + 4, dtype=torch.float32, device=dev())
+    big[1:n + 1] = T(u, torch.float32)
+    uv = big[1:n + 1]
+    assert uv.data_ptr() % 16 == 4
+    w = H(ctx.level_ax(0, uv, h1=1.0, h2=0.5, prec=prec, assemble=False))
+    ref = O.ax_local(u, lev.G, lev.B, lev.D, 1.0, 0.5).ravel()
+    assert relmax(w, ref) < tol
+    wa = H(ctx.level_ax(0, T(u, torch.float32), h1=1.0, h2=0.5, prec=prec, assemble=False))
+    assert relmax(w, wa) < 1e-6
+
+
 def test_level_ax_on_coarse_levels():
     dev()
     mesh = si.box_mesh((3, 3, 2), 7, warp=0.1, perm_seed=1, dirichlet=("x0",))

@@ -133,3 +133,14 @@ def test_default_schedule_orders():
     assert [l["N"] for l in ctx.levels] == [7, 3, 1]
     ctx1 = ctx_for(si.box_mesh(2, 1))
     assert [l["N"] for l in ctx1.levels] == [1]
+
+
+def test_measured_peaks_are_plausible():
+    """sem_measure_peaks: FP64 FMA and FP64 mma.sync near GB300's 1.25 TFLOP/s nominal FP64 rate,
+    FP32 FMA tens of TFLOP/s (the arithmetic denominators of the roofline reports)."""
+    dev()
+    from paper_2104_05829_gb300 import measure_peaks
+    p = measure_peaks()
+    print(p)
+    assert 0.3 < p["fp64_fma"] < 3.0 and 0.3 < p["fp64_mma"] < 3.0
+    assert 20.0 < p["fp32_fma"] < 200.0
