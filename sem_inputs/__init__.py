@@ -163,12 +163,8 @@ def gaussian_assembled_rhs(mesh: dict, seed: int = 0) -> np.ndarray:
     return vals[mesh["lattice"]]
 
 
-def smooth_random_field(mesh: dict, seed: int, modes: int = 64, kmax: int = 4) -> np.ndarray:
-    """g(x) = sum_m a_m cos(pi k_m . x + phi_m) at the mesh nodes.
-
-    k_m is drawn uniformly from the integer vectors with 0 < |k| <= kmax,
-    a_m ~ N(0, 2/modes) (so Var g is about 1) and phi_m ~ U[0, 2 pi).
-    """
+def smooth_random_modes(seed: int, modes: int = 64, kmax: int = 4):
+    """The draws of smooth_random_field: wave vectors k_m [modes, 3], amplitudes a_m, phases phi_m."""
     r = np.arange(-kmax, kmax + 1)
     kk = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
     n2 = (kk ** 2).sum(1)
@@ -177,6 +173,16 @@ def smooth_random_field(mesh: dict, seed: int, modes: int = 64, kmax: int = 4) -
     k = kk[pick].astype(np.float64)
     a = np.sqrt(2.0 / modes) * normal(seed + 1, np.arange(modes))
     phi = 2.0 * np.pi * uniform01(seed + 2, np.arange(modes))
+    return k, a, phi
+
+
+def smooth_random_field(mesh: dict, seed: int, modes: int = 64, kmax: int = 4) -> np.ndarray:
+    """g(x) = sum_m a_m cos(pi k_m . x + phi_m) at the mesh nodes.
+
+    k_m is drawn uniformly from the integer vectors with 0 < |k| <= kmax,
+    a_m ~ N(0, 2/modes) (so Var g is about 1) and phi_m ~ U[0, 2 pi).
+    """
+    k, a, phi = smooth_random_modes(seed, modes, kmax)
     g = np.zeros_like(mesh["x"])
     for m in range(modes):
         g += a[m] * np.cos(np.pi * (k[m, 0] * mesh["x"] + k[m, 1] * mesh["y"] + k[m, 2] * mesh["z"]) + phi[m])
