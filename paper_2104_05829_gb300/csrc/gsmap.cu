@@ -283,44 +283,6 @@ __global__ void k_seg_fill_zero(int64_t n, const int64_t* __restrict__ f, const 
 
 __global__ void k_set_last(int32_t* seg_off, int64_t q, int64_t v) { seg_off[q] = (int32_t)v; }
 
-// class of every segment: 0 = 2 copies, 1 = 4, 2 = 8 (not Dirichlet), 3 = any other
-__device__ __forceinline__ int seg_class(const int32_t* off, const uint8_t* dir, int64_t q) {
-  if (dir[q]) return 3;
-  const int m = off[q + 1] - off[q];
-  return m == 2 ? 0 : (m == 4 ? 1 : (m == 8 ? 2 : 3));
-}
-
-__global__ void k_seg_class_flags(int64_t nseg, const int32_t* __restrict__ off, const uint8_t* __restrict__ dir,
-                                  int64_t* __restrict__ f0, int64_t* __restrict__ f1, int64_t* __restrict__ f2,
-                                  int64_t* __restrict__ f3) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nseg) return;
-  const int c = seg_class(off, dir, q);
-  f0[q] = c == 0;
-  f1[q] = c == 1;
-  f2[q] = c == 2;
-  f3[q] = c == 3;
-}
-
-__global__ void k_seg_class_fill(int64_t nseg, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
-                                 const uint8_t* __restrict__ dir, const int64_t* __restrict__ p0,
-                                 const int64_t* __restrict__ p1, const int64_t* __restrict__ p2,
-                                 const int64_t* __restrict__ p3, int2* __restrict__ t2, int4* __restrict__ t4,
-                                 int4* __restrict__ t8, int32_t* __restrict__ tr) {
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nseg) return;
-  const int c = seg_class(off, dir, q);
-  const int32_t* s = idx + off[q];
-  if (c == 0) t2[p0[q]] = make_int2(s[0], s[1]);
-  else if (c == 1) t4[p1[q]] = make_int4(s[0], s[1], s[2], s[3]);
-  else if (c == 2) {
-    t8[2 * p2[q]] = make_int4(s[0], s[1], s[2], s[3]);
-    t8[2 * p2[q] + 1] = make_int4(s[4], s[5], s[6], s[7]);
-  } else {
-    tr[p3[q]] = (int32_t)q;
-  }
-}
-
 inline unsigned nblocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -451,38 +413,6 @@ int build_maps(Level& L, cudaStream_t s) {
   SEM_LAUNCH_CHECK();
   k_set_last<<<1, 1, 0, s>>>(L.seg_off, L.n_seg, L.n_seg_idx);
   SEM_LAUNCH_CHECK();
-  // segments by class, each class in canonical order
-  {
-    const int64_t ns = L.n_seg;
-    int64_t *f[4], *p[4];
-    for (int c = 0; c < 4; ++c) {
-      SEM_CUDA_TRY(cudaMallocAsync((void**)&f[c], (ns + 1) * 8, s));
-      SEM_CUDA_TRY(cudaMallocAsync((void**)&p[c], (ns + 1) * 8, s));
-    }
-    int64_t cnt[4] = {0, 0, 0, 0};
-    if (ns > 0) {
-      k_seg_class_flags<<<nblocks(ns), 256, 0, s>>>(ns, L.seg_off, L.seg_dir, f[0], f[1], f[2], f[3]);
-      SEM_LAUNCH_CHECK();
-      for (int c = 0; c < 4; ++c) SEM_TRY(scan_excl(f[c], p[c], ns, &cnt[c], s));
-    }
-    L.n_gs2 = cnt[0];
-    L.n_gs4 = cnt[1];
-    L.n_gs8 = cnt[2];
-    L.n_gsr = cnt[3];
-    MALLOC(L.gs2, cnt[0] + 1);
-    MALLOC(L.gs4, cnt[1] + 1);
-    MALLOC(L.gs8, 2 * cnt[2] + 2);
-    MALLOC(L.gsr, cnt[3] + 1);
-    if (ns > 0) {
-      k_seg_class_fill<<<nblocks(ns), 256, 0, s>>>(ns, L.seg_off, L.seg_idx, L.seg_dir, p[0], p[1], p[2], p[3],
-                                                   L.gs2, L.gs4, L.gs8, L.gsr);
-      SEM_LAUNCH_CHECK();
-    }
-    for (int c = 0; c < 4; ++c) {
-      SEM_CUDA_TRY(cudaFreeAsync(f[c], s));
-      SEM_CUDA_TRY(cudaFreeAsync(p[c], s));
-    }
-  }
   for (void* ptr : {(void*)d_bad, (void*)fnz, (void*)fz, (void*)pnz, (void*)pz, (void*)k1, (void*)k2, (void*)v1,
                     (void*)v2, (void*)head, (void*)hscan, (void*)segflag, (void*)seglen, (void*)segpos,
                     (void*)lenpos, (void*)zf, (void*)zfp})

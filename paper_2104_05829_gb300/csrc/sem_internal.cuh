@@ -87,14 +87,6 @@ struct Level {
   int32_t* seg_off = nullptr;  // [n_seg+1]
   int32_t* seg_idx = nullptr;  // [n_seg_idx]
   uint8_t* seg_dir = nullptr;  // [n_seg]
-  // the same segments grouped by class for the gather-scatter kernel: non-Dirichlet
-  // segments of 2, 4 and 8 copies as fixed-stride index tables (ascending local index
-  // within a segment, segments in canonical order), every other segment by its number
-  int2* gs2 = nullptr;         // [n_gs2]
-  int4* gs4 = nullptr;         // [n_gs4]
-  int4* gs8 = nullptr;         // [2 n_gs8]
-  int32_t* gsr = nullptr;      // [n_gsr] segment numbers
-  int64_t n_gs2 = 0, n_gs4 = 0, n_gs8 = 0, n_gsr = 0;
   // interpolation from level+1 (coarse) to this level: J[a*NPc + b] = h^c_b(xi^f_a)
   Mat64 Jc{};
   Mat32 Jcf{};

@@ -220,7 +220,7 @@ int dmalloc(T** p, size_t count) {
 
 void free_level(Level& L) {
   void* ptrs[] = {L.G, L.G32, L.G16, L.G2, L.x, L.y, L.z, L.gid, L.dflag, L.ids, L.off, L.idx, L.mult, L.node,
-                  L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.gs2, L.gs4, L.gs8, L.gsr, L.dinv, L.dinv32,
+                  L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
                   L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.pp_el_off, L.pp_el,
