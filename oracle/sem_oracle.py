@@ -509,6 +509,14 @@ def coarsen(fine: Level, Nc: int) -> Level:
     return Level(Nc, fine.E, xc, yc, zc, gc, dc)
 
 
+def coarsen_field(fine: Level, coarse: Level, fL):
+    """A nodal field of the fine level evaluated at the coarse level's GLL points, element by
+    element, the way coarsen() evaluates the coordinates (the fine interpolant at the coarse
+    points). Used for a nodal coefficient h1 on the multigrid levels."""
+    Jfc = interp_matrix(fine.xi, coarse.xi)
+    return interp_local(np.asarray(fL, dtype=np.float64).reshape(fine.x.shape), Jfc)
+
+
 def prolong(fine: Level, coarse: Level, ec):
     """P e_c = R_f Q_f^T W_f J_L Q_c e_c: interpolate every element, average the copies."""
     Jcf = interp_matrix(coarse.xi, fine.xi)    # (NPf, NPc)
@@ -933,11 +941,22 @@ class PMG:
     Jacobi-PCG coarse solve (Section 3.4, "Poisson Solve Preconditioning")."""
 
     def __init__(self, levels, h1=1.0, h2=0.0, params: MGParams | None = None):
+        """h1: a scalar, or a nodal coefficient on the fine level (an L-vector shaped like
+        levels[0].x), carried to every coarser level by coarsen_field (level by level)."""
         self.levels = levels
         self.h1, self.h2 = h1, h2
         self.p = params or MGParams()
-        self.dinv = [np.where(L.free, 1.0 / L.diag(h1, h2), 0.0) for L in levels]
-        self.ops = [(lambda v, L=L: L.apply(v, h1, h2)) for L in levels]
+        if np.ndim(h1) == 0:
+            h1s = [h1] * len(levels)
+        else:
+            h1s = [np.asarray(h1, dtype=np.float64).reshape(levels[0].x.shape)]
+            for l in range(1, len(levels)):
+                h1s.append(coarsen_field(levels[l - 1], levels[l], h1s[-1]))
+            if self.p.smoother == "asm":
+                raise ValueError("the Schwarz smoother takes a scalar h1")
+        self.h1_levels = h1s
+        self.dinv = [np.where(L.free, 1.0 / L.diag(h, h2), 0.0) for L, h in zip(levels, h1s)]
+        self.ops = [(lambda v, L=L, h=h: L.apply(v, h, h2)) for L, h in zip(levels, h1s)]
         nsm = len(levels) - 1
         if self.p.smoother == "asm":
             self.sch = [schwarz_setup(levels[l]) for l in range(nsm)]
@@ -979,7 +998,8 @@ class PMG:
 
 def solve(level: Level, b, h1=1.0, h2=0.0, tol=1e-8, maxit=1000, precond="jacobi",
           levels=None, params: MGParams | None = None) -> SolveResult:
-    """Solve R Q^T A_L Q R^T x = b: Jacobi-PCG, or flexible PCG with the p-MG V-cycle."""
+    """Solve R Q^T A_L Q R^T x = b: Jacobi-PCG, or flexible PCG with the p-MG V-cycle
+    (h1 a scalar or a nodal L-vector on `level`, which must be levels[0] for p-MG)."""
     op = lambda v: level.apply(v, h1, h2)
     if precond == "jacobi":
         dinv = np.where(level.free, 1.0 / level.diag(h1, h2), 0.0)

@@ -84,3 +84,31 @@ def test_autograd_finite_differences_4x4x4_N7():
             assert abs(fd[-1] - dd) < 1e-6 * abs(dd), (which, fd, dd)
             if which == "h1":
                 assert abs(fd[0] - dd) > 10 * abs(fd[1] - dd)
+
+
+def test_grad_h1_kernel_full_size_sampled():
+    """The gradient kernel on the 32^3, N=7 box the benchmark's differentiated solve uses:
+    per-point values of sampled elements, and the copy-summed values at their nodes, against
+    the oracle evaluated on the sample's element neighbourhood."""
+    dev()
+    import types
+    mesh = si.box_mesh(32, 7, warp=0.1, perm_seed=0)
+    ctx = ctx_for(mesh, prec_copies=0, mg_orders=[7])
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(mesh["x"].shape)
+    lam = rng.standard_normal(mesh["x"].shape)
+    ut, lt = T(u), T(lam)
+    g = H(ctx.grad_h1(ut, lt)).reshape(mesh["E"], -1)
+    gs = H(ctx.grad_h1(ut, lt, sum_copies=True)).reshape(mesh["E"], -1)
+    sample = rng.choice(mesh["E"], 24, replace=False)
+    gid = mesh["gid"].reshape(mesh["E"], -1)
+    hood = np.flatnonzero(np.isin(gid, np.unique(gid[sample])).any(axis=1))
+    G, B, _ = O.geometry(mesh["x"][hood], mesh["y"][hood], mesh["z"][hood], 7)
+    lev = types.SimpleNamespace(G=G, D=O.deriv_matrix(7))
+    ref = O.grad_h1_local(lev, u[hood], lam[hood]).reshape(hood.size, -1)
+    pos = {e: i for i, e in enumerate(hood)}
+    idx = [pos[e] for e in sample]
+    assert relmax(g[sample], ref[idx]) < 1e-12
+    sums = np.zeros(gid.max() + 1)
+    np.add.at(sums, gid[hood].ravel(), ref.ravel())
+    assert relmax(gs[sample], sums[gid[sample]]) < 1e-12

@@ -205,3 +205,50 @@ def test_adjoint_gradient_vs_assembled_derivative():
         ind[l] = 1.0
         dA = O.assemble(O.element_matrices(L.G, L.B, L.D, ind.reshape(uL.shape), 0.0), L.node, L.n_G)
         assert abs(-(lam @ dA @ u) - g[l]) < 1e-12 * max(1.0, abs(g[l]))
+
+
+def test_coarsen_field_evaluates_the_fine_interpolant_at_the_coarse_points():
+    """coarsen_field evaluates each element's fine interpolant at the coarse GLL points. On an
+    affine box a field of degree <= Nf in x, y, z is its own fine interpolant, so the coarse
+    values equal the field at the coarse points whatever the coarse order; a field of higher
+    degree is not, except at the element vertices, which are GLL points of every order."""
+    mesh = si.box_mesh((3, 2, 2), 7, warp=0.0, perm_seed=1)
+    levels = O.build_levels(mesh, [7, 3, 1])
+    deg5 = lambda L: 1.0 + 0.3 * L.x ** 5 - 0.2 * L.y * L.z ** 2 + 0.1 * L.z
+    f3 = O.coarsen_field(levels[0], levels[1], deg5(levels[0]))
+    assert np.max(np.abs(f3 - deg5(levels[1]))) < 1e-13
+    lin = lambda L: 1.0 + 0.3 * L.x - 0.2 * L.y + 0.1 * L.z
+    f1 = O.coarsen_field(levels[1], levels[2], O.coarsen_field(levels[0], levels[1], lin(levels[0])))
+    assert np.max(np.abs(f1 - lin(levels[2]))) < 1e-13
+    deg9 = lambda L: L.x ** 9 * L.y
+    assert np.max(np.abs(O.coarsen_field(levels[0], levels[1], deg9(levels[0])) - deg9(levels[1]))) > 1e-10
+    chain = O.coarsen_field(levels[1], levels[2], O.coarsen_field(levels[0], levels[1], deg9(levels[0])))
+    assert np.max(np.abs(chain - deg9(levels[2]))) < 1e-13
+
+
+def test_pmg_with_a_constant_nodal_h1_is_the_scalar_pmg():
+    mesh = si.box_mesh((3, 3, 2), 5, warp=0.1, perm_seed=4, dirichlet=("x0",))
+    levels = O.build_levels(mesh, [5, 2, 1])
+    params = O.MGParams(coarse_tol=0.0, coarse_maxit=8)
+    r = levels[0].mask(np.random.default_rng(2).standard_normal(levels[0].n_G))
+    a = O.PMG(levels, 0.7, 0.3, params)
+    b = O.PMG(levels, np.full(levels[0].x.shape, 0.7), 0.3, params)
+    assert np.allclose(a.lmax, b.lmax, rtol=1e-13)
+    za, zb = a(r), b(r)
+    assert np.max(np.abs(za - zb)) < 1e-12 * np.max(np.abs(za))
+
+
+def test_pmg_with_nodal_h1_solves_the_variable_coefficient_helmholtz_problem():
+    """FCG with the nodal-h1 p-MG and Jacobi-PCG converge to the same solution of
+    A(h1, h2) u = b with h1 = exp(0.5 g) (a smooth random field), the multigrid in far fewer
+    iterations."""
+    mesh = si.box_mesh((3, 3, 3), 5, warp=0.1, perm_seed=0)
+    levels = O.build_levels(mesh, [5, 2, 1])
+    L0 = levels[0]
+    h1 = np.exp(0.5 * si.smooth_random_field(mesh, 1)).reshape(L0.x.shape)
+    b = L0.rhs_from_nodal(si.smooth_random_field(mesh, 3).reshape(L0.x.shape))
+    jac = O.solve(L0, b, h1, 1.0, tol=1e-12, maxit=5000)
+    mg = O.solve(L0, b, h1, 1.0, tol=1e-12, maxit=200, precond="pmg", levels=levels)
+    assert jac.relres <= 1e-12 and mg.relres <= 1e-12
+    assert mg.iters < jac.iters / 3, (mg.iters, jac.iters)
+    assert np.max(np.abs(mg.x - jac.x)) < 1e-9 * np.max(np.abs(jac.x))
