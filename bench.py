@@ -701,8 +701,9 @@ def device_field(mesh: dict, seed: int, dev):
 def adjoint_bench(ctx_cls, args, dev, stream):
     """The differentiated Helmholtz solve on the warped 32^3-element N=7 box (all faces Dirichlet):
     u = A(h1, h2)^-1 b(f) with h1 = exp(0.5 g), h2 = 1, loss 1/2 sum_l B_l (u_l - t_l)^2; the forward
-    Jacobi-PCG solve, the adjoint solve and the gradient kernels (torch.autograd through the
-    hand-written adjoint), FP64, to 1e-10."""
+    solve, the adjoint solve and the gradient kernels (torch.autograd through the hand-written
+    adjoint), FP64 outer iterations to 1e-10, with Jacobi-PCG (the paper's viscous solver) and with
+    flexible PCG + p-multigrid carrying the nodal h1 (FP64 and FP32 V-cycles)."""
     import torch
 
     import sem_inputs as si
@@ -710,48 +711,54 @@ def adjoint_bench(ctx_cls, args, dev, stream):
 
     e1 = args.adjoint_elements
     mesh = si.box_mesh(e1, 7, warp=0.1, perm_seed=0)
-    ctx = ctx_cls.from_mesh(mesh, prec_copies=0, mg_orders=[7])
+    ctx = ctx_cls.from_mesh(mesh)
     h1 = torch.exp(0.5 * device_field(mesh, 1, dev))
     tgt = device_field(mesh, 2, dev)
     f = device_field(mesh, 3, dev)
     B = ctx.mass_local(torch.ones_like(f))
     tol = 1e-10
-
-    def run():
-        ft = f.clone().requires_grad_(True)
-        ht = h1.clone().requires_grad_(True)
-        u = helmholtz_solve(ctx, ft, ht, h2=1.0, tol=tol, maxit=20000)
-        loss = 0.5 * torch.sum(B * (u - tgt) ** 2)
-        loss.backward()
-        return loss, ft.grad, ht.grad
-
-    run()   # warm-up
-    torch.cuda.synchronize()
-    e0, e1_, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record(stream)
-    ft = f.clone().requires_grad_(True)
-    ht = h1.clone().requires_grad_(True)
-    u = helmholtz_solve(ctx, ft, ht, h2=1.0, tol=tol, maxit=20000)
-    loss = 0.5 * torch.sum(B * (u - tgt) ** 2)
-    e1_.record(stream)
-    loss.backward()
-    e2.record(stream)
-    e2.synchronize()
-    t_fwd, t_bwd = e0.elapsed_time(e1_) / 1e3, e1_.elapsed_time(e2) / 1e3
-    # iteration counts of the two solves (the same calls the autograd function makes)
-    _, i_fwd = ctx.solve(f, h1_L=h1, h2=1.0, tol=tol, maxit=20000, precond="jacobi")
-    g = u.detach().clone() - tgt
-    g = B * g
-    ctx.gs(g)
-    _, i_adj = ctx.solve(g, h1_L=h1, h2=1.0, tol=tol, maxit=20000, precond="jacobi", rhs="assembled")
     nG = ctx.levels[0]["nG"]
     out = {"workload": f"differentiated Helmholtz solve on the warped {e1}^3-element N=7 box, all faces Dirichlet, "
                        f"h1 = exp(0.5 g) (64 Fourier modes, seed 1), h2 = 1, f seed 3, target seed 2; "
-                       f"FP64 Jacobi-PCG forward and adjoint to {tol:g}",
-           "n_L": ctx.nL, "n_G": nG, "forward_s": t_fwd, "backward_s": t_bwd, "total_s": t_fwd + t_bwd,
-           "forward_iters": i_fwd["iters"], "adjoint_iters": i_adj["iters"],
-           "ms_per_iter": 1e3 * (t_fwd + t_bwd) / max(1, i_fwd["iters"] + i_adj["iters"]),
-           "loss": loss.item(), "grad_f_norm": ft.grad.norm().item(), "grad_h1_norm": ht.grad.norm().item()}
+                       f"FP64 outer iterations to {tol:g}, forward and adjoint",
+           "n_L": ctx.nL, "n_G": nG}
+    grads = {}
+    for name, precond, prec, op in (("jacobi", "jacobi", "fp64", False), ("pmg_fp64", "pmg", "fp64", False),
+                                    ("pmg_fp32", "pmg", "fp32", False), ("pmg_fp32_outer_pairs", "pmg", "fp32", True)):
+        def run():
+            ft = f.clone().requires_grad_(True)
+            ht = h1.clone().requires_grad_(True)
+            u = helmholtz_solve(ctx, ft, ht, h2=1.0, tol=tol, maxit=20000, precond=precond, prec=prec, outer_pairs=op)
+            loss = 0.5 * torch.sum(B * (u - tgt) ** 2)
+            return ft, ht, u, loss
+
+        ft, ht, u, loss = run()          # warm-up (and the preconditioner set-up)
+        loss.backward()
+        torch.cuda.synchronize()
+        e0, e1_, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        ft, ht, u, loss = run()
+        e1_.record(stream)
+        loss.backward()
+        e2.record(stream)
+        e2.synchronize()
+        t_fwd, t_bwd = e0.elapsed_time(e1_) / 1e3, e1_.elapsed_time(e2) / 1e3
+        # iteration counts of the two solves (the calls the autograd function makes)
+        _, i_fwd = ctx.solve(f, h1_L=h1, h2=1.0, tol=tol, maxit=20000, precond=precond, prec=prec, outer_pairs=op)
+        g = B * (u.detach() - tgt)
+        ctx.gs(g)
+        _, i_adj = ctx.solve(g, h1_L=h1, h2=1.0, tol=tol, maxit=20000, precond=precond, prec=prec, rhs="assembled",
+                             outer_pairs=op)
+        out[name] = {"forward_s": t_fwd, "backward_s": t_bwd, "total_s": t_fwd + t_bwd,
+                     "forward_iters": i_fwd["iters"], "adjoint_iters": i_adj["iters"],
+                     "ms_per_iter": 1e3 * (t_fwd + t_bwd) / max(1, i_fwd["iters"] + i_adj["iters"]),
+                     "loss": loss.item(), "outer_operator": "f32x2" if op else "f64"}
+        grads[name] = (ft.grad.clone(), ht.grad.clone())
+    ref_f, ref_h = grads["jacobi"]
+    for name in ("pmg_fp64", "pmg_fp32", "pmg_fp32_outer_pairs"):
+        gf, gh = grads[name]
+        out[name]["grad_f_rel_diff_vs_jacobi"] = ((gf - ref_f).norm() / ref_f.norm()).item()
+        out[name]["grad_h1_rel_diff_vs_jacobi"] = ((gh - ref_h).norm() / ref_h.norm()).item()
     ctx.close()
     return out
 

@@ -180,7 +180,8 @@ int sem_level_info(const sem_ctx* ctx, int level, sem_level_desc* out);
  * fine level in FP64, A^e = D^T h1 G D + h2 B (eq. Ae). With SEM_AX_PAIRS the
  * element operator runs in FP32-pair arithmetic (every value an unevaluated sum
  * of two floats, error-free TwoProduct/TwoSum; about 48 significant bits and
- * the FP32 exponent range, |values| within ~1e-30..1e30; scalar h1 only), which
+ * the FP32 exponent range, |values| within ~1e-30..1e30; a nodal h1_L is split into
+ * pairs as it is read), which
  * GB300 executes far faster than FP64 instructions. The Dirichlet entries
  * of u_L are used as given; pass a masked u_L (zero at Dirichlet nodes, as every
  * solver vector is) to apply A = R Q^T A_L Q R^T. u_L and w_L must not alias.
@@ -216,6 +217,15 @@ int sem_restrict(sem_ctx* ctx, int level, int prec, const void* rf_L, void* rc_L
  * matrix of M_ASM A (an upper bound on the real parts of its Ritz values),
  * lanczos_steps steps from the seeded start vector, in FP64. Synchronous. */
 int sem_precond_setup(sem_ctx* ctx, double h1, double h2, int prec, void* stream);
+/* sem_precond_setup for A = D^T (h1 G) D + h2 B with a nodal h1 (h1_L: DEVICE, fine-level
+ * L-vector, continuous): the fine values are carried to every coarser level by evaluating
+ * each element's fine interpolant at the coarse GLL points (as the coarse coordinates are,
+ * eq. xijk), and every level's operator, Jacobi diagonal and eigenvalue estimate use them
+ * point by point; the order-1 coarse solve gets factors with G scaled by h1. CHEBY-JAC only
+ * (the Schwarz local solves take a scalar h1: SEM_EINVAL). h1_L is copied; synchronous.
+ * sem_solve with SEM_PC_PMG and coef->h1_L sets this up itself (again whenever the h1_L
+ * pointer, h2 or the precision changes). */
+int sem_precond_setup_nodal(sem_ctx* ctx, const double* h1_L, double h2, int prec, void* stream);
 /* Chebyshev smoothing (Jacobi or Schwarz, per sem_opts.smoother) on `level` (needs sem_precond_setup): x <- S(b, x);
  * x_is_zero != 0 treats x as 0 on entry. Vectors in the V-cycle's precision. */
 int sem_cheb_smooth(sem_ctx* ctx, int level, const void* b_L, void* x_L, int x_is_zero, void* stream);
@@ -242,7 +252,9 @@ int sem_get_lmax(const sem_ctx* ctx, double* lmax, int n);
 /* Solve A u = b to ||r||/||b|| <= tol with Jacobi-PCG (SEM_PC_JACOBI) or
  * flexible PCG preconditioned by the p-MG V-cycle (SEM_PC_PMG) whose
  * smoother and levels run in `prec` (SEM_FP64, SEM_FP32, SEM_BF16G); the
- * outer iteration, residual and dot products are always FP64. f_L: nodal
+ * outer iteration, residual and dot products are always FP64. A nodal
+ * coef->h1_L works with both (p-MG: CHEBY-JAC, see sem_precond_setup_nodal) and
+ * with SEM_OUTER_PAIRS. f_L: nodal
  * function or assembled b (rhs_flags). u_L: solution (continuous L-vector).
  * Blocks until done (reads one residual norm per iteration). Errors:
  * SEM_ENOTCONV (info filled, u_L holds the last iterate), SEM_EBREAKDOWN,
@@ -368,7 +380,7 @@ int sem_partition_rcb(int32_t E, const double* cx, const double* cy, const doubl
                       int32_t* part);
 /* w_L = A_L u_L on elements e0 .. e1-1 of the fine level only (eq. Ae; other elements'
  * entries of w_L are not touched). u_L, w_L and coef->h1_L are whole L-vectors. flags 0
- * (FP64) or SEM_AX_PAIRS (FP32-pair arithmetic, scalar h1). Errors: SEM_EINVAL. */
+ * (FP64) or SEM_AX_PAIRS (FP32-pair arithmetic). Errors: SEM_EINVAL. */
 int sem_ax_elements(sem_ctx* ctx, int32_t e0, int32_t e1, const double* u_L, double* w_L, const sem_coef* coef,
                     int flags, void* stream);
 /* Interface of this rank: n global ids (HOST, each held by this context's fine level)

@@ -83,6 +83,7 @@ SIGNATURES = {
     "sem_prolong_add": (_I, [_P, _I, _I, _P, _P, _P]),
     "sem_restrict": (_I, [_P, _I, _I, _P, _P, _P]),
     "sem_precond_setup": (_I, [_P, _D, _D, _I, _P]),
+    "sem_precond_setup_nodal": (_I, [_P, _P, _D, _I, _P]),
     "sem_cheb_smooth": (_I, [_P, _I, _P, _P, _I, _P]),
     "sem_vcycle": (_I, [_P, _P, _P, _P]),
     "sem_asm_apply": (_I, [_P, _I, _I, _P, _P, _D, _D, _P]),

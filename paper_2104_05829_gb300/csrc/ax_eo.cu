@@ -301,16 +301,18 @@ int ax_eo_apply(const Level& L, const double* u, double* w, double h1, double h2
   return eo_launch<ArF64>(L, u, w, L.G, h1, h2, h1L, skip, s);
 }
 
-// FP64-accurate element operator in FP32-pair arithmetic (scalar h1).
-int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s) {
+// FP64-accurate element operator in FP32-pair arithmetic (scalar h1, or a nodal h1L, split
+// into pairs as it is read).
+int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, const double* h1L,
+                   cudaStream_t s) {
   if (!L.G2) {
     set_detail("FP32-pair factors were not built");
     return SEM_EINVAL;
   }
-  return eo_launch<ArPair>(L, u, w, L.G2, h1, h2, nullptr, nullptr, s);
+  return eo_launch<ArPair>(L, u, w, L.G2, h1, h2, h1L, nullptr, s);
 }
 
-// The element operator on elements [e0, e1) only (FP64, or FP32 pairs with a scalar h1):
+// The element operator on elements [e0, e1) only (FP64 or FP32 pairs, scalar or nodal h1):
 // the same kernels on a view of the level whose pointers start at element e0.
 int ax_eo_apply_range(const Level& L, int e0, int e1, const double* u, double* w, double h1, double h2,
                       const double* h1L, bool pairs, cudaStream_t s) {
@@ -320,11 +322,11 @@ int ax_eo_apply_range(const Level& L, int e0, int e1, const double* u, double* w
   V.E = e1 - e0;
   V.nL = (int64_t)V.E * L.NP * L.NP * L.NP;
   if (pairs) {
-    if (!L.G2 || h1L) {
-      set_detail("FP32-pair factors not built, or nodal h1 with pairs");
+    if (!L.G2) {
+      set_detail("FP32-pair factors not built");
       return SEM_EINVAL;
     }
-    return eo_launch<ArPair>(V, u + off, w + off, L.G2 + 7 * off, h1, h2, nullptr, nullptr, s);
+    return eo_launch<ArPair>(V, u + off, w + off, L.G2 + 7 * off, h1, h2, h1L ? h1L + off : nullptr, nullptr, s);
   }
   return eo_launch<ArF64>(V, u + off, w + off, L.G + 7 * off, h1, h2, h1L ? h1L + off : nullptr, nullptr, s);
 }

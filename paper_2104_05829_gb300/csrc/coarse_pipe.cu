@@ -882,9 +882,10 @@ int coarse_pipe_solve(Level& L, int prec, const void* b, void* x, const void* di
   a.sc = sc;
   a.outer_sc = outer_sc;
   a.spin = L.spin_limit;
-  if (prec == SEM_FP64) return launch_pipe<double, double>(L, L.G, a, nsm, s, used);
-  if (prec == SEM_FP32) return launch_pipe<float, float>(L, L.G32, a, nsm, s, used);
-  return launch_pipe<float, __nv_bfloat16>(L, L.G16, a, nsm, s, used);
+  // with a nodal h1 the preconditioner's coarse factors are pre-scaled (h1 = 1 here)
+  if (prec == SEM_FP64) return launch_pipe<double, double>(L, L.pc_scaled ? L.pcG : L.G, a, nsm, s, used);
+  if (prec == SEM_FP32) return launch_pipe<float, float>(L, L.pc_scaled ? L.pcG32 : L.G32, a, nsm, s, used);
+  return launch_pipe<float, __nv_bfloat16>(L, L.pc_scaled ? L.pcG16 : L.G16, a, nsm, s, used);
 }
 
 }  // namespace sem

@@ -213,7 +213,7 @@ int proj_update(Proj& P, const sem_coef* c, bool pairs, const double* x, const d
   double* v = P.X + (int64_t)P.count * P.nL;
   double* w = P.AX + (int64_t)P.count * P.nL;
   SEM_CUDA_TRY(cudaMemcpyAsync(v, src, P.nL * 8, cudaMemcpyDeviceToDevice, s));
-  if (pairs) SEM_TRY(ax_pairs_apply(L, v, w, c->h1, c->h2, s));
+  if (pairs) SEM_TRY(ax_pairs_apply(L, v, w, c->h1, c->h2, c->h1_L, s));
   else SEM_TRY(ax_apply(L, SEM_FP64, v, w, c->h1, c->h2, c->h1_L, s));
   SEM_TRY(gs_apply(L, SEM_FP64, w, true, s));
   double* sc = pscal(P);
@@ -364,7 +364,7 @@ int sem_proj_update(sem_proj* h, const sem_coef* c, int flags, const double* x, 
     return SEM_EINVAL;
   }
   const bool pairs = (flags & SEM_OUTER_PAIRS) != 0;
-  if (pairs && (c->h1_L || !P->C->lev[0].G2)) {
+  if (pairs && !P->C->lev[0].G2) {
     set_detail("sem_proj_update: SEM_OUTER_PAIRS needs scalar h1 and the pair factors");
     return SEM_EINVAL;
   }

@@ -59,6 +59,15 @@ void host_interp(int nc, const double* xi_from, int nt, const double* x_to, doub
 struct Level {
   int N = 0, NP = 0, E = 0;
   long long spin_limit = 1ll << 31;   // SM clocks a device-side wait of this level's kernels may spin
+  // nodal h1 of a preconditioner set up with a nodal coefficient: the fine values,
+  // carried level by level to the coarser GLL points (allocated on first use)
+  double* h1n = nullptr;              // [nL]
+  // the coarsest level's factors with G11..G33 times h1n (B kept), for the one-launch
+  // coarse solve, which takes a scalar h1; current while pc_scaled is set
+  double* pcG = nullptr;
+  float* pcG32 = nullptr;
+  __nv_bfloat16* pcG16 = nullptr;
+  bool pc_scaled = false;
   int64_t nL = 0, nG = 0, n_ids = 0, n_idx = 0, n_seg = 0, n_seg_idx = 0;
   Mat64 D{};                 // D_hat of this order
   Mat32 Df{};
@@ -196,6 +205,8 @@ struct Ctx {
   uint64_t pc_gen = 0;                       // bumped by every preconditioner set-up
   bool pc_graph_off = false;                 // a capture failed: direct launches from then on
   int graph_steps = 0;                       // graph replays in the current solve
+  bool pc_nodal = false;                     // the preconditioner was set up with a nodal h1
+  const double* pc_h1L = nullptr;            // the caller's fine-level h1 it was set up with
   // error flag of the one-launch coarse solve (set when a bounded wait gives up)
   int* cg_err = nullptr;                     // [1]
 };
@@ -208,6 +219,9 @@ constexpr int RED_THREADS = 256;
 // ---- ax.cu
 int ax_apply(const Level& L, int prec, const void* u, void* w, double h1, double h2, const double* h1L,
              cudaStream_t s, const double* skip = nullptr);
+// a nodal field of level F at the GLL points of the next coarser level C (setup.cu), the way
+// the coarse coordinates are formed (the fine element interpolant at the coarse points)
+int interp_nodal(const Level& F, const Level& C, const double* f, double* c, cudaStream_t s);
 int diag_local(const Level& L, double h1, double h2, const double* h1L, double* d, cudaStream_t s);
 int grad_h1_apply(const Level& L, const double* u, const double* lam, double* g, cudaStream_t s);
 int geom_compute(Level& L, int* d_bad, cudaStream_t s);
@@ -222,7 +236,8 @@ int ax_eo_apply_range(const Level& L, int e0, int e1, const double* u, double* w
 
 // ---- ax_eo.cu (FP32-pair variant)
 int pairs_build(Level& L, cudaStream_t s);
-int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, cudaStream_t s);
+int ax_pairs_apply(const Level& L, const double* u, double* w, double h1, double h2, const double* h1L,
+                   cudaStream_t s);
 
 // ---- coarse_pipe.cu: recursive coordinate bisection (host): el[0..n) goes to parts
 // part0 .. part0 + parts - 1 (el_off[part] = first position), sizes within one of each
@@ -302,7 +317,8 @@ int proj_state(const Proj& P, int* count, int* maxv, double** xbar, const double
 bool proj_belongs(const Proj& P, const Ctx* C);
 
 // ---- solve.cu
-int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s);
+// h1L: NULL for the scalar h1, else the fine-level nodal h1 (DEVICE; CHEBY-JAC only)
+int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s, const double* h1L = nullptr);
 int vcycle(Ctx& C, int prec, const double* r, double* z, cudaStream_t s);
 
 // ---- transfer (ax.cu)

@@ -224,7 +224,8 @@ void free_level(Level& L) {
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
                   L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.pp_el_off, L.pp_el,
-                  L.pp_p2n, L.pp_nd_off, L.pp_nd_src, L.pp_nd_fl, L.pp_cp_off, L.pp_cp, L.pp_xbuf, L.pp_part};
+                  L.pp_p2n, L.pp_nd_off, L.pp_nd_src, L.pp_nd_fl, L.pp_cp_off, L.pp_cp, L.pp_xbuf, L.pp_part,
+                  L.h1n, L.pcG, L.pcG32, L.pcG16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -330,6 +331,16 @@ int validate_orders(const sem_mesh* m, const sem_opts& o, std::vector<int>& orde
 }
 
 }  // namespace
+
+// a nodal field of level F at the GLL points of the next coarser level C
+int interp_nodal(const Level& F, const Level& C, const double* f, double* c, cudaStream_t s) {
+  Mat64 J{};
+  host_interp(F.NP, F.xi, C.NP, C.xi, J.a);
+  const int64_t n = C.nL;
+  k_interp_coords<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C.E, F.NP, C.NP, f, c, J);
+  SEM_LAUNCH_CHECK();
+  return SEM_OK;
+}
 
 }  // namespace sem
 

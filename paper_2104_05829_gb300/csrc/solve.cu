@@ -78,6 +78,37 @@ __global__ void k_lanczos_shift(int64_t n, double* __restrict__ vprev, double* _
   }
 }
 
+// Factors of the coarsest level with the stiffness parts scaled by the nodal h1 (point by
+// point: the GLL quadrature of h1 G), B copied, in FP64 and the low-precision copies that exist.
+__global__ void k_scale_factors(int64_t n, int np3, const double* __restrict__ G, const double* __restrict__ h1,
+                                double* __restrict__ out, float* __restrict__ out32,
+                                __nv_bfloat16* __restrict__ out16) {
+  GRID_LOOP(p, n) {
+    const int64_t e = p / np3;
+    const int loc = (int)(p - e * np3);
+    const double hp = h1[p];
+    for (int c = 0; c < 7; ++c) {
+      const int64_t q = (e * 7 + c) * np3 + loc;
+      const double v = c < 6 ? G[q] * hp : G[q];
+      out[q] = v;
+      if (out32) out32[q] = __double2float_rn(v);
+      if (out16) out16[q] = __double2bfloat16(v);
+    }
+  }
+}
+
+template <typename T>
+int alloc_once(T** p, size_t count) {
+  if (*p) return SEM_OK;
+  if (cudaMalloc((void**)p, count * sizeof(T) + 16) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_detail("cudaMalloc of %zu bytes failed (nodal preconditioner)", count * sizeof(T));
+    return SEM_ENOMEM;
+  }
+  return SEM_OK;
+}
+
 // Largest eigenvalue of the symmetric tridiagonal (a, b) by Sturm-sequence bisection.
 double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
   const int m = (int)a.size();
@@ -107,10 +138,11 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
   return 0.5 * (lo + hi);
 }
 
+// the preconditioner's operator on level l (a nodal h1 of the preconditioner replaces h1)
 int level_op(Ctx& C, int l, int prec, const void* x, void* w, double h1, double h2, cudaStream_t s,
              const double* skip = nullptr) {
   const Level& L = C.lev[l];
-  SEM_TRY(ax_apply(L, prec, x, w, h1, h2, nullptr, s, skip));
+  SEM_TRY(ax_apply(L, prec, x, w, h1, h2, C.pc_nodal ? L.h1n : nullptr, s, skip));
   return gs_apply_skip(L, prec, w, true, skip, s);
 }
 
@@ -290,7 +322,11 @@ int vcycle_level(Ctx& C, int l, int prec, cudaStream_t s) {
 
 }  // namespace
 
-int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
+int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s, const double* h1L) {
+  if (h1L && C.opts.smoother != SEM_SMOOTH_JACOBI) {
+    set_detail("a nodal h1 needs the Chebyshev-Jacobi smoother (the Schwarz local solves take a scalar h1)");
+    return SEM_EINVAL;
+  }
   if (prec != SEM_FP64 && !C.lev[0].dinv32) {
     set_detail("FP32 preconditioner copies were not built");
     return SEM_EINVAL;
@@ -305,12 +341,37 @@ int precond_setup(Ctx& C, double h1, double h2, int prec, cudaStream_t s) {
   }
   C.pc_ready = false;
   ++C.pc_gen;
+  // a nodal h1: the fine values, then each coarser level's from the level above; the
+  // level operators take it point by point (the scalar h1 becomes 1)
+  C.pc_nodal = h1L != nullptr;
+  C.pc_h1L = h1L;
+  if (h1L) {
+    h1 = 1.0;
+    for (int l = 0; l < C.nlevels; ++l) {
+      Level& L = C.lev[l];
+      SEM_TRY(alloc_once(&L.h1n, (size_t)L.nL));
+      if (l == 0) SEM_CUDA_TRY(cudaMemcpyAsync(L.h1n, h1L, L.nL * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      else SEM_TRY(interp_nodal(C.lev[l - 1], L, C.lev[l - 1].h1n, L.h1n, s));
+    }
+  }
   for (int l = 0; l < C.nlevels; ++l) {
     Level& L = C.lev[l];
-    SEM_TRY(level_dinv(C, l, h1, h2, nullptr, L.dinv, L.dinv32, s));
+    L.pc_scaled = false;
+    SEM_TRY(level_dinv(C, l, h1, h2, C.pc_nodal ? L.h1n : nullptr, L.dinv, L.dinv32, s));
     if (l == C.nlevels - 1) {
       if (C.opts.coarse_mode == SEM_COARSE_AUTO || C.opts.coarse_mode == SEM_COARSE_PIPE)
         SEM_TRY(coarse_pipe_build(L, s));
+      if (C.pc_nodal) {
+        // the one-launch coarse solve takes a scalar h1: give it h1-scaled factors
+        const size_t nf = (size_t)7 * L.nL;
+        SEM_TRY(alloc_once(&L.pcG, nf));
+        if (L.G32) SEM_TRY(alloc_once(&L.pcG32, nf));
+        if (L.G16) SEM_TRY(alloc_once(&L.pcG16, nf));
+        k_scale_factors<<<vgrid(L.nL), 256, 0, s>>>(L.nL, L.NP * L.NP * L.NP, L.G, L.h1n, L.pcG,
+                                                    L.G32 ? L.pcG32 : nullptr, L.G16 ? L.pcG16 : nullptr);
+        SEM_LAUNCH_CHECK();
+        L.pc_scaled = true;
+      }
       continue;
     }
     if (C.opts.smoother == SEM_SMOOTH_ASM) {
@@ -426,13 +487,12 @@ extern "C" {
 int sem_ax(sem_ctx* h, const double* u, double* w, const sem_coef* c, int flags, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));
-  if (!u || !w || !c || u == w || (flags & ~(SEM_AX_ASSEMBLE | SEM_AX_PAIRS)) ||
-      ((flags & SEM_AX_PAIRS) && c->h1_L)) {
-    set_detail("sem_ax: NULL or aliased vector, NULL coefficients, unknown flag, or nodal h1 with pairs");
+  if (!u || !w || !c || u == w || (flags & ~(SEM_AX_ASSEMBLE | SEM_AX_PAIRS))) {
+    set_detail("sem_ax: NULL or aliased vector, NULL coefficients or unknown flag");
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (flags & SEM_AX_PAIRS) SEM_TRY(ax_pairs_apply(C->lev[0], u, w, c->h1, c->h2, s));
+  if (flags & SEM_AX_PAIRS) SEM_TRY(ax_pairs_apply(C->lev[0], u, w, c->h1, c->h2, c->h1_L, s));
   else SEM_TRY(ax_apply(C->lev[0], SEM_FP64, u, w, c->h1, c->h2, c->h1_L, s));
   if (flags & SEM_AX_ASSEMBLE) SEM_TRY(gs_apply(C->lev[0], SEM_FP64, w, true, s));
   return SEM_OK;
@@ -458,7 +518,7 @@ int sem_level_ax(sem_ctx* h, int level, int prec, const void* u, void* w, double
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (prec == SEM_FP64P) SEM_TRY(ax_pairs_apply(C->lev[level], (const double*)u, (double*)w, h1, h2, s));
+  if (prec == SEM_FP64P) SEM_TRY(ax_pairs_apply(C->lev[level], (const double*)u, (double*)w, h1, h2, nullptr, s));
   else SEM_TRY(ax_apply(C->lev[level], prec, u, w, h1, h2, nullptr, s));
   const int vprec = (prec == SEM_FP64P) ? SEM_FP64 : prec;
   if (flags & SEM_AX_ASSEMBLE) SEM_TRY(gs_apply(C->lev[level], vprec, w, true, s));
@@ -512,6 +572,17 @@ int sem_precond_setup(sem_ctx* h, double h1, double h2, int prec, void* stream) 
   SEM_TRY(check_level(C, 0));
   SEM_TRY(check_prec(C, 0, prec));
   return precond_setup(*C, h1, h2, prec, (cudaStream_t)stream);
+}
+
+int sem_precond_setup_nodal(sem_ctx* h, const double* h1_L, double h2, int prec, void* stream) {
+  Ctx* C = ctx_of(h);
+  SEM_TRY(check_level(C, 0));
+  SEM_TRY(check_prec(C, 0, prec));
+  if (!h1_L) {
+    set_detail("sem_precond_setup_nodal: NULL h1_L");
+    return SEM_EINVAL;
+  }
+  return precond_setup(*C, 1.0, h2, prec, (cudaStream_t)stream, h1_L);
 }
 
 int sem_cheb_smooth(sem_ctx* h, int level, const void* b, void* x, int x_is_zero, void* stream) {
@@ -666,18 +737,18 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
     return SEM_EINVAL;
   }
   if (precond == SEM_PC_PMG) SEM_TRY(check_prec(C, 0, prec));
-  if (precond == SEM_PC_PMG && c->h1_L) {
-    set_detail("sem_solve: the p-multigrid preconditioner needs scalar coefficients");
+  if (precond == SEM_PC_PMG && c->h1_L && C->opts.smoother != SEM_SMOOTH_JACOBI) {
+    set_detail("sem_solve: p-multigrid with a nodal h1 needs the Chebyshev-Jacobi smoother");
     return SEM_EINVAL;
   }
   const bool pairs = (rhs_flags & SEM_OUTER_PAIRS) != 0;
-  if (pairs && (c->h1_L || !C->lev[0].G2)) {
-    set_detail("sem_solve: SEM_OUTER_PAIRS needs scalar h1 and the pair factors (SEM_BUILD_PAIRS)");
+  if (pairs && !C->lev[0].G2) {
+    set_detail("sem_solve: SEM_OUTER_PAIRS needs the pair factors (SEM_BUILD_PAIRS)");
     return SEM_EINVAL;
   }
   // outer operator R QQ^T A_L p (FP64 or FP32-pair element kernel)
   auto outer_ax = [&](const double* in, double* out, const double* skip, cudaStream_t st) -> int {
-    if (pairs) SEM_TRY(ax_pairs_apply(C->lev[0], in, out, c->h1, c->h2, st));
+    if (pairs) SEM_TRY(ax_pairs_apply(C->lev[0], in, out, c->h1, c->h2, c->h1_L, st));
     else SEM_TRY(ax_apply(C->lev[0], SEM_FP64, in, out, c->h1, c->h2, c->h1_L, st, skip));
     return gs_apply_skip(C->lev[0], SEM_FP64, out, true, skip, st);
   };
@@ -739,8 +810,11 @@ int solve_impl(Ctx* C, Proj* P, const double* f, const sem_coef* c, double tol, 
       launched += nb;
     }
   } else {
-    if (!C->pc_ready || C->pc_h1 != c->h1 || C->pc_h2 != c->h2 || C->pc_prec != prec)
-      SEM_TRY(precond_setup(*C, c->h1, c->h2, prec, s));
+    // the preconditioner is kept while the coefficients are the same (a nodal h1: the same
+    // pointer; values changed behind it give a stale but still valid preconditioner)
+    const bool same = C->pc_ready && C->pc_h2 == c->h2 && C->pc_prec == prec &&
+                      (c->h1_L ? (C->pc_nodal && C->pc_h1L == c->h1_L) : (!C->pc_nodal && C->pc_h1 == c->h1));
+    if (!same) SEM_TRY(precond_setup(*C, c->h1, c->h2, prec, s, c->h1_L));
     SEM_TRY(pcg_begin_tol(*C, L, SEM_FP64, b, x0 ? w : nullptr, u, C->r, nullptr, nullptr, sc, tol, s, bbref));
     SEM_CUDA_TRY(cudaMemsetAsync(C->p, 0, n * 8, s));
     SEM_TRY(read_scalars(*C, 0, s));

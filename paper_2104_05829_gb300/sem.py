@@ -207,9 +207,14 @@ class SemContext:
                                        self._vec(rc, level + 1, prec, "rc"), _stream(stream)), "sem_restrict")
         return rc
 
-    def precond_setup(self, h1=1.0, h2=0.0, prec="fp64", stream=None):
-        L.check(self._lib.sem_precond_setup(self._h, float(h1), float(h2), _PREC[prec], _stream(stream)),
-                "sem_precond_setup")
+    def precond_setup(self, h1=1.0, h2=0.0, prec="fp64", h1_L=None, stream=None):
+        """sem_precond_setup, or sem_precond_setup_nodal with a nodal h1_L (fine-level tensor)."""
+        if h1_L is None:
+            L.check(self._lib.sem_precond_setup(self._h, float(h1), float(h2), _PREC[prec], _stream(stream)),
+                    "sem_precond_setup")
+        else:
+            L.check(self._lib.sem_precond_setup_nodal(self._h, _dev(h1_L, torch.float64, self.nL, "h1_L"), float(h2),
+                                                      _PREC[prec], _stream(stream)), "sem_precond_setup_nodal")
         self._pc_prec = prec
 
     def cheb_smooth(self, level, b, x, x_is_zero=False, stream=None):

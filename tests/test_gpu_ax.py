@@ -171,6 +171,19 @@ def test_ax_pairs_all_orders(N):
         assert err < PAIRS_TOL, (N, err)
 
 
+@pytest.mark.parametrize("N", [3, 7])
+def test_ax_pairs_nodal_h1(N):
+    """The FP32-pair kernel with a nodal h1 (split into pairs as it is read) against the oracle."""
+    dev()
+    mesh, ctx, lev = _setup((3, 2, 5), N, seed=N + 20)
+    rng = np.random.default_rng(N)
+    u = rng.uniform(-1, 1, mesh["x"].shape)
+    h1 = np.exp(0.5 * si.smooth_random_field(mesh, 1))
+    w = H(ctx.ax(T(u), h1_L=T(h1), h2=0.5, assemble=False, pairs=True))
+    ref = O.ax_local(u, lev.G, lev.B, lev.D, h1, 0.5).ravel()
+    assert relmax(w, ref) < PAIRS_TOL
+
+
 def test_ax_pairs_smooth_field_and_level_api():
     """A smooth input (strong cancellation in D u) through the level API."""
     dev()
