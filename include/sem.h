@@ -241,7 +241,10 @@ int sem_cheb_smooth(sem_ctx* ctx, int level, const void* b_L, void* x_L, int x_i
  * Dirichlet boundary side drops its boundary node, a Neumann side keeps it).
  * W = 1 / (number of subdomain slots holding the node), 0 at Dirichlet nodes.
  * Needs 2 <= N on the level; the data are built on the first call (synchronous).
- * prec: SEM_FP64 (double vectors) or SEM_FP32 (float vectors). */
+ * prec: SEM_FP64 (double vectors), SEM_FP32 (float vectors, FP32 local solves) or
+ * SEM_BF16G (float vectors; the local solves on the TF32 tensor cores, operands
+ * rounded to 11 significant bits, FP32 accumulation: the smoother of the BF16-G
+ * V-cycle). */
 int sem_asm_apply(sem_ctx* ctx, int level, int prec, const void* r_L, void* z_L, double h1, double h2,
                   void* stream);
 /* z_L = M r_L: one V-cycle (needs sem_precond_setup), FP64 in and out. */

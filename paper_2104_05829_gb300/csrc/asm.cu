@@ -18,12 +18,15 @@
 //   l_d = (2/L_d)^2 lam_d,  c = (2/L_r)(2/L_s)(2/L_t).
 // The smoother is z = W sum_e P_e^T F_e P_e r (P_e: gather to the box,
 // P_e^T: add the own and face-layer slots back), masked; W = 1 / (number of
-// subdomain slots holding the node). Kernels: k_asm_fdm (gather, six 1-D
-// contractions with the scaling fused between the t passes, store of the own
-// part to z and the face layers to a staging array), k_asm_pull (adds the
-// staged face-layer values to the nodes they belong to, in a fixed order),
-// then gs and the weighted Chebyshev update.
+// subdomain slots holding the node). Kernels: k_asm_fdm or k_asm_fdm_tc (gather,
+// six 1-D contractions with the scaling fused between the t passes, store of the
+// own part to z and the face layers to a staging array), k_asm_sum (for every
+// node that has several copies, receives staged face-layer values or is
+// Dirichlet: the sum of its copies and of its staged values in a fixed order,
+// written to every copy, zero at Dirichlet nodes; P^T and QQ^T in one pass),
+// then the weighted Chebyshev update.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -400,16 +403,451 @@ __global__ void __launch_bounds__(AsmShape<NP>::THREADS, (asm_min_blocks<T, NP>(
   }
 }
 
-// z[pts[q]] += sum of the staged face-layer values that belong to that local point
-template <typename T>
-__global__ void k_asm_pull(int64_t npts, const int32_t* __restrict__ pts, const int32_t* __restrict__ off,
-                           const int32_t* __restrict__ src, const T* __restrict__ zf, T* __restrict__ z) {
-  GRID_LOOP(q, npts) {
-    const int32_t pnt = pts[q];
-    T acc = z[pnt];
-    for (int32_t o = off[q]; o < off[q + 1]; ++o) acc += zf[src[o]];
-    z[pnt] = acc;
+// ---------------------------------------------------------------------------
+// Tensor-core form of the FDM local solves (FP32 data, TF32 mma.sync with FP32
+// accumulation). One warp per element. Each of the six 1-D passes is the product
+//   OUT[l][a] = sum_m IN[l][m] Q[m][a]     (Q = S forward, S^T inverse)
+// over the M^2 lines l = (p, q) of the box (p the line's fast coordinate, q its
+// slow one), issued as mma.m16n8k8 on OUT^T = Q^T IN^T: the A operand is Q^T
+// (rows a and the contraction index m padded to 16 with zeros, loaded once per
+// pass), the B operand is a tile of eight lines. Tiles (TcPlan): eight lines of
+// one q (p = 8h .. 8h+7), and, when M = 8 P + R with R = 2 or 4, the R remaining
+// lines of 8/R consecutive q; for other R the rows are padded to whole tiles.
+// Every lane then reads and writes at a fixed offset from its own base in every
+// tile, so the addresses of a fully unrolled pass are immediates.
+// A pass reads a line-major buffer ((p + M q) LS + m) and writes each lane's two
+// accumulator lines (p, p + 1 of one q) as one 64-bit word of the next pass's
+// layout, whose contraction index is this pass's p. Lines (p, q) per pass: r
+// (j, k), s (k, i), t and inverse t (j, i), inverse s (i, k), inverse r (j, k);
+// the inverse t pass reads an index-major buffer (m LD + p + M q, LD = 8 mod 32)
+// and the result lands index-major for the output loops. LS = 12 (or 20) puts
+// the 32 lanes of a load on distinct banks (64-bit: each bank twice).
+// SPLIT = 1: one TF32 product per term (operands rounded to 11 significant
+// bits); SPLIT = 3: each operand as the sum of two TF32 numbers and three
+// products (hi*hi + hi*lo + lo*hi), about FP32 accuracy.
+// Warps per block (1..8) that put the most warps on an SM within 227 KB of shared memory
+// (blocks of ref + w * per_warp bytes, plus 1 KB reserved per block).
+constexpr int tc_warps_per_block(int ref, int per_warp) {
+  int best = 1, most = 0;
+  for (int w = 1; w <= 8; ++w) {
+    const int bytes = ref + w * per_warp;
+    if (bytes > 227 * 1024) break;
+    const int warps = w * ((227 * 1024) / (bytes + 1024));
+    if (warps > most) {
+      most = warps;
+      best = w;
+    }
   }
+  return best;
+}
+
+template <int NP>
+struct TcShape {
+  static constexpr int M = NP + 2;
+  static constexpr int L = M * M;                        // lines of one pass
+  static constexpr int KS = (M + 7) / 8;                 // k-steps of the contraction index
+  static constexpr int LS = M <= 12 ? 12 : 20;           // line stride
+  static constexpr int LD = L + ((8 - L % 32) + 32) % 32;   // index stride, = 8 mod 32
+  static constexpr int BUF0 = L * LS > M * LD ? L * LS : M * LD;
+  static constexpr int BUF = (BUF0 + 3) / 4 * 4;
+  static constexpr int TAB = (L + 3) / 4 * 4;
+  static constexpr int WARP_FLOATS = 2 * BUF + TAB;      // two buffers and the scaling table
+  static constexpr int REFB = 9 * AsmShape<NP>::REF * 4;
+  static constexpr int WPB = tc_warps_per_block(REFB, WARP_FLOATS * 4);   // elements (warps) per block
+  static constexpr size_t SMEM = (size_t)REFB + (size_t)WPB * WARP_FLOATS * 4;
+};
+
+template <int NP>
+struct TcPlan {
+  static constexpr int M = NP + 2, PM = M / 8, R = M % 8;
+  static constexpr bool LEFT = R == 2 || R == 4;             // remainder lines grouped over q
+  static constexpr bool PAD = !(R == 0 || LEFT);             // rows padded to whole tiles
+  static constexpr int PB = PAD ? PM + 1 : PM;               // tiles of one q
+  static constexpr int RT = LEFT ? 8 / R : 1;                // q per remainder tile
+  static constexpr int NMT = M * PB;
+  static constexpr int NTT = NMT + (LEFT ? (M + RT - 1) / RT : 0);
+};
+
+// FP32 -> TF32 operand: round to 11 significant bits (half away from zero in magnitude) with
+// two integer operations; the tensor cores read the top 19 bits of the word.
+__device__ __forceinline__ uint32_t tf32_rn(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void tf32_split(float x, uint32_t& h, uint32_t& l) {
+  h = tf32_rn(x);
+  if (SPLIT == 3) l = tf32_rn(x - __uint_as_float(h));   // x - h is exact
+}
+
+// Q^T as the A operand of every k-step: a0 = Q[m(t)][g], a1 = Q[m(t)][g+8], a2 = Q[m'(t)][g],
+// a3 = Q[m'(t)][g+8]; PERM pairs the contraction indices as m = 8ks + 2t, m' = m + 1 (so that
+// the B operand's two words per lane are adjacent), otherwise m = 8ks + t, m' = m + 4.
+template <int NP, bool TRANS, bool PERM, int SPLIT>
+__device__ __forceinline__ void tc_qfrag(const float* __restrict__ S, int g, int t,
+                                         uint32_t (&ah)[TcShape<NP>::KS][4], uint32_t (&al)[TcShape<NP>::KS][4]) {
+  constexpr int M = TcShape<NP>::M, MR = AsmShape<NP>::MR;
+  auto q = [&](int m, int a) -> float {
+    if (m >= M || a >= M) return 0.f;
+    return TRANS ? S[a * MR + m] : S[m * MR + a];
+  };
+#pragma unroll
+  for (int ks = 0; ks < TcShape<NP>::KS; ++ks) {
+    const int m0 = PERM ? 8 * ks + 2 * t : 8 * ks + t;
+    const int m1 = PERM ? m0 + 1 : m0 + 4;
+    tf32_split<SPLIT>(q(m0, g), ah[ks][0], al[ks][0]);
+    tf32_split<SPLIT>(q(m0, g + 8), ah[ks][1], al[ks][1]);
+    tf32_split<SPLIT>(q(m1, g), ah[ks][2], al[ks][2]);
+    tf32_split<SPLIT>(q(m1, g + 8), ah[ks][3], al[ks][3]);
+  }
+}
+
+template <int SPLIT>
+__device__ __forceinline__ void tc_mma(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], float x0,
+                                       float x1) {
+  uint32_t bh0, bl0, bh1, bl1;
+  tf32_split<SPLIT>(x0, bh0, bl0);
+  tf32_split<SPLIT>(x1, bh1, bl1);
+  if (SPLIT == 3) {
+    mma_tf32(c, al, bh0, bh1);
+    mma_tf32(c, ah, bl0, bl1);
+  }
+  mma_tf32(c, ah, bh0, bh1);
+}
+
+// Lines of tile tt for lane (g, t): the B operand's line (bp, bq), and the first of the two
+// accumulator lines (sp, sq) (the second is sp + 1, same sq).
+template <int NP>
+__device__ __forceinline__ void tc_tile(int tt, int g, int t, int& bp, int& bq, int& sp, int& sq) {
+  using P = TcPlan<NP>;
+  if constexpr (P::LEFT) {
+    if (tt >= P::NMT) {
+      const int q0 = (tt - P::NMT) * P::RT;
+      bq = q0 + g / P::R;
+      bp = 8 * P::PM + g % P::R;
+      sq = q0 + (2 * t) / P::R;
+      sp = 8 * P::PM + (2 * t) % P::R;
+      return;
+    }
+  }
+  const int q = tt / P::PB, h = tt - q * P::PB;
+  bq = sq = q;
+  bp = 8 * h + g;
+  sp = 8 * h + 2 * t;
+}
+
+// B operand loads from line-major buffers: the two words of a lane as one 64-bit load (m = 2t,
+// 2t + 1; a half-warp then spans its banks twice at LS = 12) or as two 32-bit loads (m = t,
+// t + 4; every lane on its own bank).
+constexpr bool kTcPairLoads = false;
+
+// the B operand of one tile (zero for lines or indices outside the box)
+template <int NP, bool IN_LINE>
+__device__ __forceinline__ void tc_load(const float* __restrict__ in, int bp, int bq, int t,
+                                        float (&x)[TcShape<NP>::KS][2]) {
+  using Sh = TcShape<NP>;
+  constexpr int M = Sh::M, LS = Sh::LS, LD = Sh::LD;
+  const bool ok = bp < M && bq < M;
+  const int l = bp + M * bq;
+#pragma unroll
+  for (int ks = 0; ks < Sh::KS; ++ks) {
+    x[ks][0] = 0.f;
+    x[ks][1] = 0.f;
+    if (IN_LINE && kTcPairLoads) {
+      const int m0 = 8 * ks + 2 * t;
+      if (ok && m0 + 1 < M) {
+        const float2 v = *reinterpret_cast<const float2*>(in + l * LS + m0);
+        x[ks][0] = v.x;
+        x[ks][1] = v.y;
+      } else if (ok && m0 < M) {
+        x[ks][0] = in[l * LS + m0];
+      }
+    } else if (IN_LINE) {
+      const int m0 = 8 * ks + t;
+      if (ok && m0 < M) x[ks][0] = in[l * LS + m0];
+      if (ok && m0 + 4 < M) x[ks][1] = in[l * LS + m0 + 4];
+    } else {
+      const int m0 = 8 * ks + t;
+      if (ok && m0 < M) x[ks][0] = in[m0 * LD + l];
+      if (ok && m0 + 4 < M) x[ks][1] = in[(m0 + 4) * LD + l];
+    }
+  }
+}
+
+// One pass over every tile, fully unrolled; the operands of the next tile are loaded before
+// this tile's products and stores. post(sp, sq, c): c[0], c[1] = OUT[(sp, sq)][g],
+// OUT[(sp + 1, sq)][g]; c[2], c[3] the same for output g + 8.
+template <int NP, int SPLIT, bool IN_LINE, class Post>
+__device__ __forceinline__ void tc_pass(const float* __restrict__ in, const uint32_t (&ah)[TcShape<NP>::KS][4],
+                                        const uint32_t (&al)[TcShape<NP>::KS][4], int g, int t, Post post) {
+  using Sh = TcShape<NP>;
+  using P = TcPlan<NP>;
+  float xn[Sh::KS][2];
+  {
+    int bp, bq, sp, sq;
+    tc_tile<NP>(0, g, t, bp, bq, sp, sq);
+    tc_load<NP, IN_LINE>(in, bp, bq, t, xn);
+  }
+#pragma unroll
+  for (int tt = 0; tt < P::NTT; ++tt) {
+    float x[Sh::KS][2];
+#pragma unroll
+    for (int ks = 0; ks < Sh::KS; ++ks) {
+      x[ks][0] = xn[ks][0];
+      x[ks][1] = xn[ks][1];
+    }
+    int bp, bq, sp, sq;
+    if (tt + 1 < P::NTT) {
+      tc_tile<NP>(tt + 1, g, t, bp, bq, sp, sq);
+      tc_load<NP, IN_LINE>(in, bp, bq, t, xn);
+    }
+    tc_tile<NP>(tt, g, t, bp, bq, sp, sq);
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ks = 0; ks < Sh::KS; ++ks) tc_mma<SPLIT>(c, ah[ks], al[ks], x[ks][0], x[ks][1]);
+    post(sp, sq, c);
+  }
+}
+
+// Store OUT[(p, q)][a] and OUT[(p + 1, q)][a] at addr(p, q, a), addr(p, q, a) + 1 (p is the
+// next layout's fastest index): one 64-bit word when M is even, else two words.
+template <int NP, class Addr>
+__device__ __forceinline__ void tc_store_pair(float* __restrict__ out, int p, int q, int a, float v0, float v1,
+                                              Addr addr) {
+  constexpr int M = TcShape<NP>::M;
+  if (a >= M || q >= M || p >= M) return;
+  if (M % 2 == 0) {
+    *reinterpret_cast<float2*>(out + addr(p, q, a)) = make_float2(v0, v1);
+  } else {
+    out[addr(p, q, a)] = v0;
+    if (p + 1 < M) out[addr(p, q, a) + 1] = v1;
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ void layer_coords(int f, int a, int b, int& ib, int& jb, int& kb) {
+  const int d = f >> 1, c = (f & 1) ? NP + 1 : 0;
+  if (d == 0) { ib = c; jb = a + 1; kb = b + 1; }
+  else if (d == 1) { ib = a + 1; jb = c; kb = b + 1; }
+  else { ib = a + 1; jb = b + 1; kb = c; }
+}
+
+template <int NP, int SPLIT>
+__global__ void __launch_bounds__(32 * TcShape<NP>::WPB)
+    k_asm_fdm_tc(int E, const float* __restrict__ bv, const float* __restrict__ wv,
+                 const int32_t* __restrict__ layer, const uint8_t* __restrict__ bt, const float* __restrict__ len,
+                 const float* __restrict__ ref, float h1, float h2, float* __restrict__ z, float* __restrict__ zf) {
+  using Sh = TcShape<NP>;
+  using As = AsmShape<NP>;
+  constexpr int M = Sh::M, L = Sh::L, LS = Sh::LS, LD = Sh::LD, KS = Sh::KS, MR = As::MR;
+  constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+  extern __shared__ __align__(16) float s_tc[];
+  float* s_ref = s_tc;                    // 9 side combinations (REF is a multiple of 4)
+  float* s_warp = s_tc + 9 * As::REF;     // per warp: B0, B1, the scaling table
+  for (int q = threadIdx.x; q < 9 * As::REF; q += blockDim.x) s_ref[q] = ref[q];
+  __syncthreads();
+  const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int e = blockIdx.x * Sh::WPB + wq;
+  if (e >= E) return;   // no block-wide barrier follows
+  float* B0 = s_warp + wq * Sh::WARP_FLOATS;
+  float* B1 = B0 + Sh::BUF;
+  float* base = B1 + Sh::BUF;   // h1 (l_r + l_s) + h2 per line (j, i) of the t pass
+  for (int q = lane; q < Sh::BUF / 4; q += 32) reinterpret_cast<float4*>(B0)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const uint8_t* b6 = bt + (size_t)e * 6;
+  const float* Sr = s_ref + (3 * b6[0] + b6[1]) * As::REF;
+  const float* Ss = s_ref + (3 * b6[2] + b6[3]) * As::REF;
+  const float* St = s_ref + (3 * b6[4] + b6[5]) * As::REF;
+  const float sr = 2.f / len[(size_t)e * 3 + 0], ss = 2.f / len[(size_t)e * 3 + 1], st = 2.f / len[(size_t)e * 3 + 2];
+  for (int l = lane; l < L; l += 32) {
+    const int i = l / M, j = l - i * M;
+    base[l] = h1 * (Sr[M * MR + i] * sr * sr + Ss[M * MR + j] * ss * ss) + h2;
+  }
+  __syncwarp();
+  // gather the box (r pass layout: (j + M k) LS + i), the loads of a chunk (all of them up to
+  // N = 7) issued before the first store
+  {
+    constexpr int NO = (NP3 + 31) / 32, NF = (6 * NP2 + 31) / 32;
+    constexpr int CO = NO < 16 ? NO : 16, CF = NF < 12 ? NF : 12;
+    constexpr int IO = (NO + CO - 1) / CO, IF = (NF + CF - 1) / CF, NI = IO > IF ? IO : IF;
+    const size_t eb = (size_t)e * NP3;
+    const int32_t* lay = layer + (size_t)e * 6 * NP2;
+#pragma unroll 1
+    for (int it = 0; it < NI; ++it) {
+      const int o0 = it * CO, f0 = it * CF;   // this chunk's own-point and face-layer slots
+      float ob[CO], ow[CO];
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        const int q = lane + 32 * (o0 + c);
+        ob[c] = q < NP3 ? bv[eb + q] : 0.f;
+        ow[c] = (wv && q < NP3) ? wv[eb + q] : 0.f;
+      }
+      int32_t src[CF];
+#pragma unroll
+      for (int c = 0; c < CF; ++c) {
+        const int q = lane + 32 * (f0 + c);
+        src[c] = q < 6 * NP2 ? lay[q] : -1;
+      }
+      float fb[CF], fw[CF];
+#pragma unroll
+      for (int c = 0; c < CF; ++c) {
+        fb[c] = src[c] >= 0 ? bv[src[c]] : 0.f;
+        fw[c] = (wv && src[c] >= 0) ? wv[src[c]] : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < CO; ++c) {
+        const int q = lane + 32 * (o0 + c);
+        if (q < NP3) {
+          const int k = q / NP2, j = (q / NP) % NP, i = q % NP;
+          B0[((j + 1) + M * (k + 1)) * LS + i + 1] = ob[c] - ow[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CF; ++c) {
+        const int q = lane + 32 * (f0 + c);
+        if (src[c] >= 0) {
+          const int f = q / NP2, ab = q - f * NP2;
+          int ib, jb, kb;
+          layer_coords<NP>(f, ab / NP, ab % NP, ib, jb, kb);
+          B0[(jb + M * kb) * LS + ib] = fb[c] - fw[c];
+        }
+      }
+    }
+  }
+  __syncwarp();
+  uint32_t ah[KS][4], al[KS][4];
+  // next layout (q + M a) LS + p: the s pass after r, the inverse s pass after inverse t
+  auto ad_qa = [](int p, int q, int a) { return (q + M * a) * LS + p; };
+  // next layout (a + M q) LS + p: the t pass after s, the inverse r pass after inverse s
+  auto ad_aq = [](int p, int q, int a) { return (a + M * q) * LS + p; };
+  // index-major a LD + p + M q: the inverse t pass after t, and the result
+  auto ad_im = [](int p, int q, int a) { return a * LD + p + M * q; };
+  // r: lines (j, k)
+  tc_qfrag<NP, false, kTcPairLoads, SPLIT>(Sr, g, t, ah, al);
+  tc_pass<NP, SPLIT, true>(B0, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+    tc_store_pair<NP>(B1, p, q, g, c[0], c[1], ad_qa);
+    tc_store_pair<NP>(B1, p, q, g + 8, c[2], c[3], ad_qa);
+  });
+  __syncwarp();
+  // s: lines (k, i)
+  tc_qfrag<NP, false, kTcPairLoads, SPLIT>(Ss, g, t, ah, al);
+  tc_pass<NP, SPLIT, true>(B1, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+    tc_store_pair<NP>(B0, p, q, g, c[0], c[1], ad_aq);
+    tc_store_pair<NP>(B0, p, q, g + 8, c[2], c[3], ad_aq);
+  });
+  __syncwarp();
+  // t: lines (j, i), scaled by c / (h1 (l_r + l_s + l_t) + h2)
+  {
+    const float cc = sr * ss * st;
+    const float ht0 = g < M ? h1 * St[M * MR + g] * st * st : 0.f;
+    const float ht1 = g + 8 < M ? h1 * St[M * MR + g + 8] * st * st : 0.f;
+    tc_qfrag<NP, false, kTcPairLoads, SPLIT>(St, g, t, ah, al);
+    tc_pass<NP, SPLIT, true>(B0, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+      if (p >= M || q >= M) return;
+      const int l = p + M * q;
+      const float b0 = base[l], b1 = p + 1 < M ? base[l + 1] : 1.f;
+      const float dn[4] = {b0 + ht0, b1 + ht0, b0 + ht1, b1 + ht1};
+      float v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = dn[k] != 0.f ? fdiv(cc * c[k], dn[k]) : 0.f;
+      tc_store_pair<NP>(B1, p, q, g, v[0], v[1], ad_im);
+      tc_store_pair<NP>(B1, p, q, g + 8, v[2], v[3], ad_im);
+    });
+  }
+  __syncwarp();
+  // inverse t: lines (j, i), index-major input
+  tc_qfrag<NP, true, false, SPLIT>(St, g, t, ah, al);
+  tc_pass<NP, SPLIT, false>(B1, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+    tc_store_pair<NP>(B0, p, q, g, c[0], c[1], ad_qa);
+    tc_store_pair<NP>(B0, p, q, g + 8, c[2], c[3], ad_qa);
+  });
+  __syncwarp();
+  // inverse s: lines (i, k)
+  tc_qfrag<NP, true, kTcPairLoads, SPLIT>(Ss, g, t, ah, al);
+  tc_pass<NP, SPLIT, true>(B0, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+    tc_store_pair<NP>(B1, p, q, g, c[0], c[1], ad_aq);
+    tc_store_pair<NP>(B1, p, q, g + 8, c[2], c[3], ad_aq);
+  });
+  __syncwarp();
+  // inverse r: lines (j, k) -> the result, index-major i LD + j + M k
+  tc_qfrag<NP, true, kTcPairLoads, SPLIT>(Sr, g, t, ah, al);
+  tc_pass<NP, SPLIT, true>(B1, ah, al, g, t, [&](int p, int q, const float (&c)[4]) {
+    tc_store_pair<NP>(B0, p, q, g, c[0], c[1], ad_im);
+    tc_store_pair<NP>(B0, p, q, g + 8, c[2], c[3], ad_im);
+  });
+  __syncwarp();
+  // outputs, unrolled so that the slot arithmetic folds into per-lane constants
+  const size_t eb = (size_t)e * NP3;
+#pragma unroll
+  for (int c = 0; c < (NP3 + 31) / 32; ++c) {
+    const int q = lane + 32 * c;
+    if (q < NP3) {
+      const int k = q / NP2, j = (q / NP) % NP, i = q % NP;
+      z[eb + q] = B0[(i + 1) * LD + (j + 1) + M * (k + 1)];
+    }
+  }
+  float* zfe = zf + (size_t)e * 6 * NP2;
+#pragma unroll
+  for (int c = 0; c < (6 * NP2 + 31) / 32; ++c) {
+    const int q = lane + 32 * c;
+    if (q < 6 * NP2) {
+      const int f = q / NP2, ab = q - f * NP2;
+      int ib, jb, kb;
+      layer_coords<NP>(f, ab / NP, ab % NP, ib, jb, kb);
+      zfe[q] = B0[ib * LD + jb + M * kb];
+    }
+  }
+}
+
+// Threads [0, nw): for every work node w, s = sum of its items in list order (item >= 0: the
+// local copy z[item]; item < 0: the staged face-layer value zf[-item - 1]), written to every
+// copy; 0 at Dirichlet nodes. The copies of a node come first, ascending, then the staged slots
+// of each copy. Threads [nw, nw + np): the nodes with one copy and one staged value, as
+// (copy, slot) pairs: z[copy] += zf[slot].
+template <typename T>
+__global__ void k_asm_sum(int64_t nw, const int32_t* __restrict__ off, const int32_t* __restrict__ item,
+                          const uint8_t* __restrict__ dir, int64_t np, const int2* __restrict__ pair,
+                          const T* __restrict__ zf, T* __restrict__ z) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= nw) {
+    if (w < nw + np) {
+      const int2 cs = pair[w - nw];
+      z[cs.x] = z[cs.x] + zf[cs.y];
+    }
+    return;
+  }
+  const int b = off[w], e = off[w + 1], m = e - b;
+  if (dir[w]) {
+    for (int p = b; p < e; ++p)
+      if (item[p] >= 0) z[item[p]] = T(0);
+    return;
+  }
+  if (m <= 8) {
+    int id[8];
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) id[q] = q < m ? item[b + q] : 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = q < m ? (id[q] >= 0 ? z[id[q]] : zf[-id[q] - 1]) : T(0);
+    T s = v[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q)
+      if (q < m) s += v[q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < m && id[q] >= 0) z[id[q]] = s;
+    return;
+  }
+  T s = T(0);
+  for (int p = b; p < e; ++p) {
+    const int it = item[p];
+    s += it >= 0 ? z[it] : zf[-it - 1];
+  }
+  for (int p = b; p < e; ++p)
+    if (item[p] >= 0) z[item[p]] = s;
 }
 
 template <typename T>
@@ -454,11 +892,30 @@ inline unsigned vgrid2(int64_t n) {
   return (unsigned)b;
 }
 
+// tc (FP32 data only): 0 the FP32 FMA kernel, 1 TF32 tensor cores, 3 three TF32 products.
 template <typename T, int NP>
-int launch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, double h2, cudaStream_t s) {
+int launch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, double h2, int tc, cudaStream_t s) {
   using Sh = AsmShape<NP>;
   const T* len = std::is_same<T, double>::value ? (const T*)L.sch_len : (const T*)L.sch_len32;
   const T* ref = std::is_same<T, double>::value ? (const T*)L.sch_ref : (const T*)L.sch_ref32;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc) {
+      using Tc = TcShape<NP>;
+      const unsigned grid = (unsigned)((L.E + Tc::WPB - 1) / Tc::WPB);
+      static PerDevice<bool> attr[2];
+      if (tc == 3) {
+        SEM_TRY(smem_attr_once(attr[1], (const void*)k_asm_fdm_tc<NP, 3>, Tc::SMEM));
+        k_asm_fdm_tc<NP, 3><<<grid, 32 * Tc::WPB, Tc::SMEM, s>>>(L.E, b, w, L.sch_layer, L.sch_bt, len, ref,
+                                                                 (float)h1, (float)h2, z, zf);
+      } else {
+        SEM_TRY(smem_attr_once(attr[0], (const void*)k_asm_fdm_tc<NP, 1>, Tc::SMEM));
+        k_asm_fdm_tc<NP, 1><<<grid, 32 * Tc::WPB, Tc::SMEM, s>>>(L.E, b, w, L.sch_layer, L.sch_bt, len, ref,
+                                                                 (float)h1, (float)h2, z, zf);
+      }
+      SEM_LAUNCH_CHECK();
+      return SEM_OK;
+    }
+  }
   const unsigned grid = (unsigned)((L.E + Sh::EPB - 1) / Sh::EPB);
   k_asm_fdm<T, NP><<<grid, Sh::THREADS, 0, s>>>(L.E, b, w, L.sch_layer, L.sch_bt, len, ref, (T)h1, (T)h2, z, zf);
   SEM_LAUNCH_CHECK();
@@ -466,18 +923,19 @@ int launch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, d
 }
 
 template <typename T>
-int dispatch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, double h2, cudaStream_t s) {
+int dispatch_fdm(const Level& L, const T* b, const T* w, T* z, T* zf, double h1, double h2, int tc,
+                 cudaStream_t s) {
   switch (L.NP) {
-    case 3: return launch_fdm<T, 3>(L, b, w, z, zf, h1, h2, s);
-    case 4: return launch_fdm<T, 4>(L, b, w, z, zf, h1, h2, s);
-    case 5: return launch_fdm<T, 5>(L, b, w, z, zf, h1, h2, s);
-    case 6: return launch_fdm<T, 6>(L, b, w, z, zf, h1, h2, s);
-    case 7: return launch_fdm<T, 7>(L, b, w, z, zf, h1, h2, s);
-    case 8: return launch_fdm<T, 8>(L, b, w, z, zf, h1, h2, s);
-    case 9: return launch_fdm<T, 9>(L, b, w, z, zf, h1, h2, s);
-    case 10: return launch_fdm<T, 10>(L, b, w, z, zf, h1, h2, s);
-    case 11: return launch_fdm<T, 11>(L, b, w, z, zf, h1, h2, s);
-    case 12: return launch_fdm<T, 12>(L, b, w, z, zf, h1, h2, s);
+    case 3: return launch_fdm<T, 3>(L, b, w, z, zf, h1, h2, tc, s);
+    case 4: return launch_fdm<T, 4>(L, b, w, z, zf, h1, h2, tc, s);
+    case 5: return launch_fdm<T, 5>(L, b, w, z, zf, h1, h2, tc, s);
+    case 6: return launch_fdm<T, 6>(L, b, w, z, zf, h1, h2, tc, s);
+    case 7: return launch_fdm<T, 7>(L, b, w, z, zf, h1, h2, tc, s);
+    case 8: return launch_fdm<T, 8>(L, b, w, z, zf, h1, h2, tc, s);
+    case 9: return launch_fdm<T, 9>(L, b, w, z, zf, h1, h2, tc, s);
+    case 10: return launch_fdm<T, 10>(L, b, w, z, zf, h1, h2, tc, s);
+    case 11: return launch_fdm<T, 11>(L, b, w, z, zf, h1, h2, tc, s);
+    case 12: return launch_fdm<T, 12>(L, b, w, z, zf, h1, h2, tc, s);
     default:
       set_detail("the Schwarz smoother needs 2 <= N <= 11 (level order %d)", L.N);
       return SEM_EINVAL;
@@ -604,6 +1062,40 @@ int schwarz_build(Ctx& C, Level& L, cudaStream_t s) {
   std::vector<int32_t> pfill(poff.begin(), poff.end() - 1);
   for (size_t t = 0; t < layer.size(); ++t)
     if (layer[t] >= 0) psrc[pfill[first[layer[t]]]++] = (int32_t)t;
+  // work nodes of k_asm_sum: every node with several copies, staged values or a Dirichlet mask,
+  // in the order of their first copies (neighbouring threads then touch neighbouring points);
+  // items: its copies (ascending), then the staged slots of each copy (slot order)
+  std::vector<int32_t> woff(1, 0), witem, wpair;
+  std::vector<uint8_t> wdir;
+  for (int64_t l = 0; l < nL; ++l) {
+    const int64_t g = node[l];
+    const int64_t c0 = hoff[g], c1 = hoff[g + 1];
+    if (hidx[c0] != l) continue;
+    bool pulled = false;
+    for (int64_t o = c0; o < c1; ++o) pulled = pulled || first[hidx[o]] >= 0;
+    const bool dirichlet = dmask[hidx[c0]] != 0;
+    if (c1 - c0 < 2 && !pulled && !dirichlet) continue;
+    if (c1 - c0 == 1 && !dirichlet) {
+      const int64_t f = first[hidx[c0]];
+      if (poff[f + 1] - poff[f] == 1) {   // one copy, one staged value: a (copy, slot) pair
+        wpair.push_back((int32_t)hidx[c0]);
+        wpair.push_back(psrc[poff[f]]);
+        continue;
+      }
+    }
+    for (int64_t o = c0; o < c1; ++o) witem.push_back((int32_t)hidx[o]);
+    for (int64_t o = c0; o < c1; ++o) {
+      const int64_t f = first[hidx[o]];
+      if (f < 0) continue;
+      for (int32_t q = poff[f]; q < poff[f + 1]; ++q) witem.push_back(-psrc[q] - 1);
+    }
+    if (witem.size() > (size_t)INT32_MAX) {
+      set_detail("Schwarz work lists exceed 2^31 entries");
+      return SEM_EINVAL;
+    }
+    woff.push_back((int32_t)witem.size());
+    wdir.push_back(dirichlet ? 1 : 0);
+  }
   // reference 1-D data for the nine side combinations
   // packed per combination as S rows of stride MR (a multiple of 4), then lam
   const int MR = (M + 3) / 4 * 4, REF = M * MR + MR;
@@ -627,22 +1119,25 @@ int schwarz_build(Ctx& C, Level& L, cudaStream_t s) {
   SEM_TRY(dmalloc_n(&L.sch_ref, ref.size()));
   SEM_TRY(dmalloc_n(&L.sch_w, (size_t)nL));
   SEM_TRY(dmalloc_n(&L.sch_zf, layer.size()));
-  SEM_TRY(dmalloc_n(&L.sch_pts, pts.size()));
-  SEM_TRY(dmalloc_n(&L.sch_poff, poff.size()));
-  SEM_TRY(dmalloc_n(&L.sch_psrc, psrc.size()));
+  SEM_TRY(dmalloc_n(&L.sch_woff, woff.size()));
+  SEM_TRY(dmalloc_n(&L.sch_witem, witem.size()));
+  SEM_TRY(dmalloc_n(&L.sch_wdir, wdir.size()));
+  SEM_TRY(dmalloc_n(&L.sch_wpair, wpair.size() / 2));
   if (f32) {
     SEM_TRY(dmalloc_n(&L.sch_len32, (size_t)E * 3));
     SEM_TRY(dmalloc_n(&L.sch_ref32, ref32.size()));
     SEM_TRY(dmalloc_n(&L.sch_w32, (size_t)nL));
     SEM_TRY(dmalloc_n(&L.sch_zf32, layer.size()));
   }
-  L.sch_npts = (int64_t)pts.size();
+  L.sch_nw = (int64_t)wdir.size();
+  L.sch_np = (int64_t)wpair.size() / 2;
   SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_layer, layer.data(), layer.size() * 4, cudaMemcpyHostToDevice, s));
   SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_bt, bt.data(), bt.size(), cudaMemcpyHostToDevice, s));
   SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_ref, ref.data(), ref.size() * 8, cudaMemcpyHostToDevice, s));
-  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_pts, pts.data(), pts.size() * 4, cudaMemcpyHostToDevice, s));
-  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_poff, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice, s));
-  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_psrc, psrc.data(), psrc.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_woff, woff.data(), woff.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_witem, witem.data(), witem.size() * 4, cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_wdir, wdir.data(), wdir.size(), cudaMemcpyHostToDevice, s));
+  SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_wpair, wpair.data(), wpair.size() * 4, cudaMemcpyHostToDevice, s));
   if (f32) SEM_CUDA_TRY(cudaMemcpyAsync(L.sch_ref32, ref32.data(), ref32.size() * 4, cudaMemcpyHostToDevice, s));
   k_elem_lengths<<<(unsigned)((E * 3 + 255) / 256), 256, 0, s>>>((int)E, NP, L.x, L.y, L.z, L.sch_len,
                                                                    f32 ? L.sch_len32 : nullptr);
@@ -667,6 +1162,9 @@ int schwarz_build(Ctx& C, Level& L, cudaStream_t s) {
   return SEM_OK;
 }
 
+// FP32 local solves: the FMA kernel (0), or TF32 tensor cores with one (1) or three (3) products.
+constexpr int kFdmFp32Mode = 3;
+
 // z = sum_e P_e^T F_e P_e (b - w) on level L, gathered over copies and masked
 // (no weight). w may be null (r = b). prec: SEM_FP64 (double) or FP32 (float vectors).
 int asm_sum(const Level& L, int prec, const void* b, const void* w, void* z, double h1, double h2, cudaStream_t s) {
@@ -674,21 +1172,25 @@ int asm_sum(const Level& L, int prec, const void* b, const void* w, void* z, dou
     set_detail("Schwarz data of level order %d not built", L.N);
     return SEM_EINVAL;
   }
+  const unsigned nb = (unsigned)((L.sch_nw + L.sch_np + 255) / 256);
   if (prec == SEM_FP64) {
-    SEM_TRY(dispatch_fdm<double>(L, (const double*)b, (const double*)w, (double*)z, L.sch_zf, h1, h2, s));
-    k_asm_pull<double><<<vgrid2(L.sch_npts), 256, 0, s>>>(L.sch_npts, L.sch_pts, L.sch_poff, L.sch_psrc, L.sch_zf,
-                                                          (double*)z);
+    SEM_TRY(dispatch_fdm<double>(L, (const double*)b, (const double*)w, (double*)z, L.sch_zf, h1, h2, 0, s));
+    if (nb)
+      k_asm_sum<double><<<nb, 256, 0, s>>>(L.sch_nw, L.sch_woff, L.sch_witem, L.sch_wdir, L.sch_np, L.sch_wpair,
+                                           L.sch_zf, (double*)z);
   } else {
     if (!L.sch_ref32) {
       set_detail("FP32 Schwarz data not built (no FP32 factor copies)");
       return SEM_EINVAL;
     }
-    SEM_TRY(dispatch_fdm<float>(L, (const float*)b, (const float*)w, (float*)z, L.sch_zf32, h1, h2, s));
-    k_asm_pull<float><<<vgrid2(L.sch_npts), 256, 0, s>>>(L.sch_npts, L.sch_pts, L.sch_poff, L.sch_psrc, L.sch_zf32,
-                                                         (float*)z);
+    const int tc = prec == SEM_BF16G ? 1 : kFdmFp32Mode;
+    SEM_TRY(dispatch_fdm<float>(L, (const float*)b, (const float*)w, (float*)z, L.sch_zf32, h1, h2, tc, s));
+    if (nb)
+      k_asm_sum<float><<<nb, 256, 0, s>>>(L.sch_nw, L.sch_woff, L.sch_witem, L.sch_wdir, L.sch_np, L.sch_wpair,
+                                          L.sch_zf32, (float*)z);
   }
   SEM_LAUNCH_CHECK();
-  return gs_apply(L, prec, z, true, s);
+  return SEM_OK;
 }
 
 int asm_weight(const Level& L, int prec, void* z, cudaStream_t s) {

@@ -120,10 +120,11 @@ struct Level {
   float* sch_w32 = nullptr;
   double* sch_zf = nullptr;       // [E][6][NP*NP] staged face-layer outputs
   float* sch_zf32 = nullptr;
-  int32_t* sch_pts = nullptr;     // local points that receive face-layer outputs
-  int32_t* sch_poff = nullptr;    // CSR offsets into sch_psrc
-  int32_t* sch_psrc = nullptr;    // staged slots per point, in slot order
-  int64_t sch_npts = 0;
+  int32_t* sch_woff = nullptr;    // [nw+1] CSR offsets of the work nodes of the Schwarz sum
+  int32_t* sch_witem = nullptr;   // copies (local index >= 0), then staged slots (-slot - 1)
+  uint8_t* sch_wdir = nullptr;    // [nw] Dirichlet work nodes (written as zero)
+  int2* sch_wpair = nullptr;      // [np] (copy, slot) of the nodes with one copy and one staged value
+  int64_t sch_nw = 0, sch_np = 0;
   // sub-domain coarse solve (coarse_pipe.cu; built on first use at order 1)
   int pp_blocks = 0;              // sub-domains, one block each; 0 not built, -1 does not apply
   int pp_max_el = 0, pp_max_nd = 0, pp_max_cp = 0;   // largest sub-domain: elements, nodes, copy entries

@@ -223,7 +223,7 @@ void free_level(Level& L) {
                   L.label, L.dmask, L.owner, L.cwt, L.cwt32, L.seg_off, L.seg_idx, L.seg_dir, L.dinv, L.dinv32,
                   L.vb, L.vx, L.vr, L.vd, L.vw, L.fb, L.fx, L.fr, L.fd, L.fw, L.cp, L.cpf,
                   L.sch_layer, L.sch_bt, L.sch_len, L.sch_len32, L.sch_ref, L.sch_ref32, L.sch_w, L.sch_w32,
-                  L.sch_zf, L.sch_zf32, L.sch_pts, L.sch_poff, L.sch_psrc, L.pp_el_off, L.pp_el,
+                  L.sch_zf, L.sch_zf32, L.sch_woff, L.sch_witem, L.sch_wdir, L.sch_wpair, L.pp_el_off, L.pp_el,
                   L.pp_p2n, L.pp_nd_off, L.pp_nd_src, L.pp_nd_fl, L.pp_cp_off, L.pp_cp, L.pp_xbuf, L.pp_part,
                   L.h1n, L.pcG, L.pcG32, L.pcG16};
   for (void* p : ptrs)

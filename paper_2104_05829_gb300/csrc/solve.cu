@@ -598,12 +598,12 @@ int sem_cheb_smooth(sem_ctx* h, int level, const void* b, void* x, int x_is_zero
 int sem_asm_apply(sem_ctx* h, int level, int prec, const void* r, void* z, double h1, double h2, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, level));
-  if (!r || !z || r == z || (prec != SEM_FP64 && prec != SEM_FP32)) {
-    set_detail("sem_asm_apply: NULL or aliased vector, or precision other than SEM_FP64/SEM_FP32");
+  if (!r || !z || r == z || (prec != SEM_FP64 && prec != SEM_FP32 && prec != SEM_BF16G)) {
+    set_detail("sem_asm_apply: NULL or aliased vector, or precision other than SEM_FP64/SEM_FP32/SEM_BF16G");
     return SEM_EINVAL;
   }
   Level& L = C->lev[level];
-  if (prec == SEM_FP32 && !L.G32 && !L.G16) {
+  if (prec != SEM_FP64 && !L.G32 && !L.G16) {
     set_detail("sem_asm_apply: FP32 copies were not built");
     return SEM_EINVAL;
   }

@@ -47,6 +47,27 @@ def test_asm_apply_matches_oracle_on_every_smoothed_level(N, orders):
             assert relmax(z32, _gL(Lo, ref)) < 2e-5, (l, h1, h2)
 
 
+@pytest.mark.parametrize("N,orders", [(5, (5, 2, 1)), (7, (7, 3, 1))])
+def test_asm_apply_tf32_tensor_cores_match_oracle(N, orders):
+    """The BF16-G V-cycle's Schwarz application: the FDM local solves as TF32 tensor-core
+    products (operands rounded to 11 significant bits, FP32 accumulation), on levels with an
+    even box edge (N = 7, 3: paired stores) and an odd one (N = 5, 2), all side types and 18
+    elements (not a multiple of the four elements of a block)."""
+    dev()
+    mesh, ctx, levels = _mg_pair(shape=(3, 2, 3), N=N, orders=orders, dirichlet=("x0", "z1"))
+    rng = np.random.default_rng(10 + N)
+    for l, Lo in enumerate(levels[:-1]):
+        sch = O.schwarz_setup(Lo)
+        r = Lo.mask(rng.standard_normal(Lo.n_G))
+        for h1, h2 in ((1.0, 0.0), (0.7, 2.5)):
+            ref = _gL(Lo, O.asm_apply(Lo, sch, r, h1, h2))
+            z = H(ctx.asm_apply(l, T(_gL(Lo, r), torch.float32), h1=h1, h2=h2, prec="bf16g"))
+            err_max = relmax(z, ref)
+            err_2 = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+            print(f"N={Lo.N} h1={h1} h2={h2}: TF32 Schwarz error {err_max:.2e} (max) {err_2:.2e} (2-norm)")
+            assert err_max < 2e-2 and err_2 < 5e-3, (l, h1, h2, err_max, err_2)
+
+
 def test_asm_apply_full_neumann_box_and_single_element():
     dev()
     for mesh in (si.box_mesh(2, 4, warp=0.1, perm_seed=1, dirichlet=()), si.box_mesh(1, 6, warp=0.0)):
