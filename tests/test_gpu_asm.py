@@ -68,6 +68,29 @@ def test_asm_apply_tf32_tensor_cores_match_oracle(N, orders):
             assert err_max < 2e-2 and err_2 < 5e-3, (l, h1, h2, err_max, err_2)
 
 
+@pytest.mark.parametrize("N", [8, 9, 10, 11])
+def test_asm_apply_high_orders_every_precision_match_oracle(N):
+    """Box edges M = N + 3 = 11..14: the tensor-core tile plans with padded rows (M = 11, 13, 14)
+    and with grouped remainder lines (M = 12), one and two k-steps, and the largest shared-memory
+    blocks; FP64, FP32 (three TF32 products) and TF32 (BF16-G) against the oracle on a 3x2x2 box
+    (12 elements) with Dirichlet and Neumann sides."""
+    dev()
+    mesh = si.box_mesh((3, 2, 2), N, warp=0.1, perm_seed=4, dirichlet=("x0",))
+    ctx = ctx_for(mesh, mg_orders=[N], smoother="asm")
+    Lo = O.level_from_mesh(mesh)
+    sch = O.schwarz_setup(Lo)
+    r = Lo.mask(np.random.default_rng(N).standard_normal(Lo.n_G))
+    ref = _gL(Lo, O.asm_apply(Lo, sch, r, 0.8, 1.5))
+    z = H(ctx.asm_apply(0, T(_gL(Lo, r)), h1=0.8, h2=1.5))
+    assert relmax(z, ref) < 1e-12
+    z32 = H(ctx.asm_apply(0, T(_gL(Lo, r), torch.float32), h1=0.8, h2=1.5, prec="fp32"))
+    assert relmax(z32, ref) < 2e-5
+    zt = H(ctx.asm_apply(0, T(_gL(Lo, r), torch.float32), h1=0.8, h2=1.5, prec="bf16g"))
+    err_max, err_2 = relmax(zt, ref), np.linalg.norm(zt - ref) / np.linalg.norm(ref)
+    print(f"N={N}: FP32 {relmax(z32, ref):.2e}, TF32 {err_max:.2e} (max) {err_2:.2e} (2-norm)")
+    assert err_max < 2e-2 and err_2 < 5e-3
+
+
 def test_asm_apply_full_neumann_box_and_single_element():
     dev()
     for mesh in (si.box_mesh(2, 4, warp=0.1, perm_seed=1, dirichlet=()), si.box_mesh(1, 6, warp=0.0)):
