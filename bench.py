@@ -633,6 +633,7 @@ def proj_bench(ctx_cls, args, dev):
             iters.append(info["iters"])
             rel0.append(info.get("relres0", 1.0))
         out[name] = {"mean_s": float(np.mean(times)), "mean_s_after_3": float(np.mean(times[3:])),
+                     "median_s": float(np.median(times)),
                      "iters": iters, "relres0": rel0, "times_s": times}
         if proj is not None:
             proj.close()

@@ -239,6 +239,55 @@ __global__ void k_cheb_first(int64_t n, const T* __restrict__ b, const T* __rest
   }
 }
 
+// The FP32 forms in chunks of four (16-byte aligned vectors).
+__global__ void k_cheb_first4(int64_t n, const float* __restrict__ b, const float* __restrict__ w,
+                              float* __restrict__ x, float* __restrict__ d, const float* __restrict__ dinv,
+                              float inv_theta, int x_zero) {
+  auto one = [&](float bl, float wl, float dil, float xl) {
+    const float dl = inv_theta * (dil * (w ? bl - wl : bl));
+    return make_float2(dl, x_zero ? dl : xl + dl);
+  };
+  grid_loop_f4(
+      n,
+      [&](int64_t i) {
+        const float4 bb = ld4(b, i), di = ld4(dinv, i);
+        const float4 ww = w ? ld4(w, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 xx = x_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(x, i);
+        const float2 r0 = one(bb.x, ww.x, di.x, xx.x), r1 = one(bb.y, ww.y, di.y, xx.y);
+        const float2 r2 = one(bb.z, ww.z, di.z, xx.z), r3 = one(bb.w, ww.w, di.w, xx.w);
+        st4(d, i, make_float4(r0.x, r1.x, r2.x, r3.x));
+        st4(x, i, make_float4(r0.y, r1.y, r2.y, r3.y));
+      },
+      [&](int64_t l) {
+        const float2 r = one(b[l], w ? w[l] : 0.f, dinv[l], x_zero ? 0.f : x[l]);
+        d[l] = r.x;
+        x[l] = r.y;
+      });
+}
+
+__global__ void k_cheb_step4(int64_t n, const float* __restrict__ b, const float* __restrict__ w,
+                             float* __restrict__ x, float* __restrict__ d, const float* __restrict__ dinv, float c1,
+                             float c2) {
+  auto one = [&](float bl, float wl, float dl0, float dil, float xl) {
+    const float dl = c1 * dl0 + c2 * (dil * (bl - wl));
+    return make_float2(dl, xl + dl);
+  };
+  grid_loop_f4(
+      n,
+      [&](int64_t i) {
+        const float4 bb = ld4(b, i), ww = ld4(w, i), dd = ld4(d, i), di = ld4(dinv, i), xx = ld4(x, i);
+        const float2 r0 = one(bb.x, ww.x, dd.x, di.x, xx.x), r1 = one(bb.y, ww.y, dd.y, di.y, xx.y);
+        const float2 r2 = one(bb.z, ww.z, dd.z, di.z, xx.z), r3 = one(bb.w, ww.w, dd.w, di.w, xx.w);
+        st4(d, i, make_float4(r0.x, r1.x, r2.x, r3.x));
+        st4(x, i, make_float4(r0.y, r1.y, r2.y, r3.y));
+      },
+      [&](int64_t l) {
+        const float2 r = one(b[l], w[l], d[l], dinv[l], x[l]);
+        d[l] = r.x;
+        x[l] = r.y;
+      });
+}
+
 // later steps: d = c1 d + c2 dinv (b - w); x += d
 template <typename T>
 __global__ void k_cheb_step(int64_t n, const T* __restrict__ b, const T* __restrict__ w, T* __restrict__ x,
@@ -429,6 +478,9 @@ int cheb_first(const Level& L, int prec, const void* b, const void* w, void* x, 
   if (prec == SEM_FP64)
     k_cheb_first<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
                                                      (double*)d, L.dinv, inv_theta, x_zero ? 1 : 0);
+  else if (kVec4 && aligned16({b, w, x, d, L.dinv32}))
+    k_cheb_first4<<<vgrid(L.nL / 4), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
+                                                  L.dinv32, (float)inv_theta, x_zero ? 1 : 0);
   else
     k_cheb_first<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
                                                     L.dinv32, (float)inv_theta, x_zero ? 1 : 0);
@@ -441,6 +493,9 @@ int cheb_step(const Level& L, int prec, const void* b, const void* w, void* x, v
   if (prec == SEM_FP64)
     k_cheb_step<double><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const double*)b, (const double*)w, (double*)x,
                                                     (double*)d, L.dinv, c1, c2);
+  else if (kVec4 && aligned16({b, w, x, d, L.dinv32}))
+    k_cheb_step4<<<vgrid(L.nL / 4), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
+                                                 L.dinv32, (float)c1, (float)c2);
   else
     k_cheb_step<float><<<vgrid(L.nL), 256, 0, s>>>(L.nL, (const float*)b, (const float*)w, (float*)x, (float*)d,
                                                    L.dinv32, (float)c1, (float)c2);

@@ -7,6 +7,9 @@
 // does not depend on block scheduling. Nothing spins.
 #pragma once
 
+#include <cstdint>
+#include <initializer_list>
+
 #include "sem_internal.cuh"
 
 namespace sem {
@@ -106,6 +109,28 @@ __device__ __forceinline__ void grid_loop_u(int64_t n, Ld ld, Op op) {
     for (int u = 0; u < U; ++u) op(l + u * S, v[u]);
   }
   for (; l < n; l += S) op(l, ld(l));
+}
+
+// Grid-stride loop over n floats in chunks of four: op4(i) handles elements 4i .. 4i+3 (the
+// caller's pointers are 16-byte aligned), op1(l) each element of the tail.
+template <class Op4, class Op1>
+__device__ __forceinline__ void grid_loop_f4(int64_t n, Op4 op4, Op1 op1) {
+  const int64_t n4 = n / 4, S = (int64_t)gridDim.x * blockDim.x, t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < n4; i += S) op4(i);
+  for (int64_t l = 4 * n4 + t0; l < n; l += S) op1(l);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p, int64_t i) { return reinterpret_cast<const float4*>(p)[i]; }
+__device__ __forceinline__ void st4(float* p, int64_t i, float4 v) { reinterpret_cast<float4*>(p)[i] = v; }
+
+// FP32 vector kernels in chunks of four where the vectors allow it
+constexpr bool kVec4 = true;
+
+// true when every non-null pointer is 16-byte aligned
+inline bool aligned16(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (p && ((uintptr_t)p & 15)) return false;
+  return true;
 }
 
 }  // namespace sem
