@@ -312,7 +312,10 @@ int sem_solve_proj(sem_ctx* ctx, sem_proj* pj, const double* f_L, const sem_coef
  * node, Q Q^T C_L u (SEM_ADV_ASSEMBLE; no Dirichlet mask: the term is explicit).
  * c_L: 3 DEVICE L-vectors back to back ([3][nL], components x, y, z); u_L and w_L:
  * ncomp L-vectors back to back ([ncomp][nL]); w_L must not alias c_L or u_L.
- * prec SEM_FP64 (double vectors) or SEM_FP32 (float vectors, FP32 arithmetic).
+ * prec SEM_FP64 (double vectors), SEM_FP64P (double vectors, the operator in FP32-pair
+ * arithmetic: about 48 significant bits, FP32 exponent range; the pair copies of the
+ * cubature factors, 9 nq^3 float2 per element, are built on the first such call) or SEM_FP32
+ * (float vectors, FP32 arithmetic).
  * The cubature factors w J dr/dx at the Gauss points are built on the first call
  * (synchronous; 9 nq^3 values per element in FP64 and FP32). Compiled for 2 <= N <= 8. */
 #define SEM_ADV_LOCAL 0
@@ -327,7 +330,8 @@ int sem_advect(sem_ctx* ctx, int prec, const void* c_L, const void* u_L, void* w
  * (no boundary condition is imposed: winds tangent to the walls need none). The
  * wind is linear in time between c0 (at t0) and c1 (at t1); c1 = NULL freezes it at c0.
  * c0_L, c1_L: [3][nL]; w_L: ncomp L-vectors [ncomp][nL], continuous, updated in place
- * (must not alias the winds). prec SEM_FP64 / SEM_FP32. Workspace (3 ncomp + 3
+ * (must not alias the winds). prec SEM_FP64 / SEM_FP64P (the operator in FP32 pairs, the
+ * Runge-Kutta stages in FP64) / SEM_FP32. Workspace (3 ncomp + 3
  * L-vectors) and the inverse mass are allocated on first use and kept. */
 int sem_char_advance(sem_ctx* ctx, int prec, const void* c0_L, const void* c1_L, void* w_L, int ncomp, double t0,
                      double t1, int nsub, void* stream);

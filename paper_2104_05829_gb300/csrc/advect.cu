@@ -22,11 +22,54 @@
 #include <cmath>
 #include <vector>
 
+#include "pairs.cuh"
 #include "sem_internal.cuh"
 
 namespace sem {
 
 namespace {
+
+// Arithmetics of the advection kernel: V the working value, S the stored vectors (c, u, w), G
+// the stored cubature factors and 1-D matrices. Plain FMA in FP64 or FP32; or FP32 pairs
+// (pairs.cuh, about 48 significant bits) on FP64 vectors with pre-split factors, normalised
+// (norm) wherever a value is next used as a factor.
+template <typename T>
+struct AdvPlain {
+  using V = T;
+  using S = T;
+  using G = T;
+  static constexpr bool kNorm = false;
+  __device__ static V ld(const S* p, size_t i) { return p[i]; }
+  __device__ static void st(S* p, size_t i, V v) { p[i] = v; }
+  __device__ static V lg(const G* p, size_t i) { return p[i]; }
+  __device__ static V zero() { return T(0); }
+  __device__ static V mac(V acc, V a, V b) { return fma(a, b, acc); }
+  __device__ static V mul(V a, V b) { return a * b; }
+  __device__ static V add(V a, V b) { return a + b; }
+  __device__ static V sub(V a, V b) { return a - b; }
+  __device__ static V norm(V a) { return a; }
+  static V host(double x) { return (T)x; }
+};
+
+struct AdvPair {
+  using V = ff;
+  using S = double;
+  using G = float2;
+  static constexpr bool kNorm = true;
+  __device__ static V ld(const S* p, size_t i) { return ff_split(p[i]); }
+  __device__ static void st(S* p, size_t i, V v) { p[i] = ff_join(v); }
+  __device__ static V lg(const G* p, size_t i) {
+    const float2 g = p[i];
+    return {g.x, g.y};
+  }
+  __device__ static V zero() { return {0.f, 0.f}; }
+  __device__ static V mac(V acc, V a, V b) { return ff_mac(acc, a, b); }
+  __device__ static V mul(V a, V b) { return ff_mul(a, b); }
+  __device__ static V add(V a, V b) { return ff_add(a, b); }
+  __device__ static V sub(V a, V b) { return ff_sub(a, b); }
+  __device__ static V norm(V a) { return ff_norm(a); }
+  static V host(double x) { return ff_host_split(x); }
+};
 
 // Gauss-Legendre nodes (ascending) and weights: roots of P_n by Newton's method
 // from x = cos(pi (4i - 1) / (4n + 2)), weights 2 / ((1 - x^2) P_n'(x)^2).
@@ -86,26 +129,28 @@ struct AdvShape {
   static constexpr int PS = NQ * RS;                     // plane stride
 };
 
-// dynamic shared memory of k_advect<T, NP>
-template <typename T, int NP>
+// dynamic shared memory of k_advect<Ar, NP>
+template <class Ar, int NP>
 constexpr size_t advect_smem() {
   constexpr int NQ = AdvShape<NP>::NQ, PS = AdvShape<NP>::PS;
-  return sizeof(T) * ((size_t)NQ * NP + NQ * NQ + NP * NP * NP + NP * NP * NQ + 2 * NQ * PS + 3 * NQ * NQ * NQ);
+  return sizeof(typename Ar::V) * ((size_t)NQ * NP + NQ * NQ + NP * NP * NP + NP * NP * NQ + 2 * NQ * PS + 3 * NQ * NQ * NQ);
 }
 
 // 1-D operators in shared memory: Im [NQ][NP] (GLL -> Gauss), Dq [NQ][NQ]
-template <typename T, int NP, int NQ>
-__device__ __forceinline__ void load_ops(const T* __restrict__ Im, const T* __restrict__ Dq, T* sI, T* sD) {
-  for (int q = threadIdx.x; q < NQ * NP; q += blockDim.x) sI[q] = Im[q];
-  for (int q = threadIdx.x; q < NQ * NQ; q += blockDim.x) sD[q] = Dq[q];
+template <class Ar, int NP, int NQ>
+__device__ __forceinline__ void load_ops(const typename Ar::G* __restrict__ Im, const typename Ar::G* __restrict__ Dq,
+                                         typename Ar::V* sI, typename Ar::V* sD) {
+  for (int q = threadIdx.x; q < NQ * NP; q += blockDim.x) sI[q] = Ar::lg(Im, q);
+  for (int q = threadIdx.x; q < NQ * NQ; q += blockDim.x) sD[q] = Ar::lg(Dq, q);
 }
 
 // Interpolate the element's nodal field src (in shared memory, [k][j][i]) to the
 // Gauss points; thread (a, b) receives its t-line out[c] = f(z_a, z_b, z_c).
 // Uses t1 [NP][NP][NQ] in shared memory.
-template <typename T, int NP, int NQ>
-__device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, const T* cI, int a, int b,
-                                         T (&out)[NQ]) {
+template <class Ar, int NP, int NQ>
+__device__ __forceinline__ void to_gauss(const typename Ar::V* src, typename Ar::V* t1, const typename Ar::V* sI,
+                                         const typename Ar::V* cI, int a, int b, typename Ar::V (&out)[NQ]) {
+  using T = typename Ar::V;
   // r-pass: t1[k][j][a] for j < NP (threads with b < NP); row a of I held in registers
   if (b < NP) {
     T ia[NP];
@@ -113,10 +158,10 @@ __device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, const
     for (int i = 0; i < NP; ++i) ia[i] = sI[a * NP + i];
 #pragma unroll 2
     for (int k = 0; k < NP; ++k) {
-      T acc = T(0);
+      T acc = Ar::zero();
 #pragma unroll
-      for (int i = 0; i < NP; ++i) acc = fma(ia[i], src[(k * NP + b) * NP + i], acc);
-      t1[(k * NP + b) * NQ + a] = acc;
+      for (int i = 0; i < NP; ++i) acc = Ar::mac(acc, ia[i], src[(k * NP + b) * NP + i]);
+      t1[(k * NP + b) * NQ + a] = Ar::norm(acc);
     }
   }
   __syncthreads();
@@ -128,19 +173,19 @@ __device__ __forceinline__ void to_gauss(const T* src, T* t1, const T* sI, const
     for (int j = 0; j < NP; ++j) ib[j] = sI[b * NP + j];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      T acc = T(0);
+      T acc = Ar::zero();
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc = fma(ib[j], t1[(k * NP + j) * NQ + a], acc);
-      t2[k] = acc;
+      for (int j = 0; j < NP; ++j) acc = Ar::mac(acc, ib[j], t1[(k * NP + j) * NQ + a]);
+      t2[k] = Ar::norm(acc);
     }
   }
   // t-pass in registers (cI: the interpolation matrix at compile-time indices)
 #pragma unroll
   for (int c = 0; c < NQ; ++c) {
-    T acc = T(0);
+    T acc = Ar::zero();
 #pragma unroll
-    for (int k = 0; k < NP; ++k) acc = fma(cI[c * NP + k], t2[k], acc);
-    out[c] = acc;
+    for (int k = 0; k < NP; ++k) acc = Ar::mac(acc, cI[c * NP + k], t2[k]);
+    out[c] = Ar::norm(acc);
   }
 }
 
@@ -159,32 +204,34 @@ struct AdvOps {
   T ep[H * H], op[H * H], mc[H > 0 ? H : 1], mr[H > 0 ? H : 1];
 };
 
-template <typename T, int NP>
-__device__ __forceinline__ void eo_deriv(const AdvOps<T, NP>& P, const T (&v)[nq_of(NP)], T (&o)[nq_of(NP)]) {
+template <class Ar, int NP>
+__device__ __forceinline__ void eo_deriv(const AdvOps<typename Ar::V, NP>& P, const typename Ar::V (&v)[nq_of(NP)],
+                                         typename Ar::V (&o)[nq_of(NP)]) {
+  using T = typename Ar::V;
   constexpr int NQ = nq_of(NP), H = NQ / 2, N = NQ - 1;
   T sm[H], df[H];
 #pragma unroll
   for (int b = 0; b < H; ++b) {
-    sm[b] = v[b] + v[N - b];
-    df[b] = v[b] - v[N - b];
+    sm[b] = Ar::add(v[b], v[N - b]);
+    df[b] = Ar::sub(v[b], v[N - b]);
   }
 #pragma unroll
   for (int a = 0; a < H; ++a) {
-    T ev = T(0), od = T(0);
+    T ev = Ar::zero(), od = Ar::zero();
 #pragma unroll
     for (int b = 0; b < H; ++b) {
-      ev = fma(P.ep[a * H + b], sm[b], ev);
-      od = fma(P.op[a * H + b], df[b], od);
+      ev = Ar::mac(ev, P.ep[a * H + b], sm[b]);
+      od = Ar::mac(od, P.op[a * H + b], df[b]);
     }
-    if (NQ % 2 == 1) ev = fma(P.mc[a], v[H], ev);
-    o[a] = ev + od;
-    o[N - a] = od - ev;
+    if (NQ % 2 == 1) ev = Ar::mac(ev, P.mc[a], v[H]);
+    o[a] = Ar::add(ev, od);
+    o[N - a] = Ar::sub(od, ev);
   }
   if (NQ % 2 == 1) {
-    T m = T(0);
+    T m = Ar::zero();
 #pragma unroll
-    for (int b = 0; b < H; ++b) m = fma(P.mr[b], df[b], m);
-    o[H] = m;
+    for (int b = 0; b < H; ++b) m = Ar::mac(m, P.mr[b], df[b]);
+    o[H] = Ar::norm(m);
   }
 }
 
@@ -192,19 +239,20 @@ __device__ __forceinline__ void eo_deriv(const AdvOps<T, NP>& P, const T (&v)[nq
 // warps per SM, 96 registers with a 128-byte spill: measured 1.63 ms against 1.74 ms at
 // three blocks with no spill on the 32^3 box), two at N = 8; two in FP64 (a few hundred
 // bytes of spills, measured 1.26x faster at N = 7 than one block with no spills)
-template <typename T, int NP>
+template <class Ar, int NP>
 __host__ __device__ constexpr int adv_min_blocks() {
-  return sizeof(T) == 4 ? (NP <= 8 ? 4 : 2) : 2;
+  return sizeof(typename Ar::V) == 4 ? (NP <= 8 ? 4 : 2) : 2;
 }
 
-template <typename T, int NP>
-__global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
-    k_advect(int E, int ncomp, int64_t nL, const T* __restrict__ cv, const T* __restrict__ uv,
-             const T* __restrict__ Gq, const T* __restrict__ Im, const T* __restrict__ Dq, T* __restrict__ wv,
-             AdvOps<T, NP> P) {
+template <class Ar, int NP>
+__global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<Ar, NP>()))
+    k_advect(int E, int ncomp, int64_t nL, const typename Ar::S* __restrict__ cv, const typename Ar::S* __restrict__ uv,
+             const typename Ar::G* __restrict__ Gq, const typename Ar::G* __restrict__ Im,
+             const typename Ar::G* __restrict__ Dq, typename Ar::S* __restrict__ wv, AdvOps<typename Ar::V, NP> P) {
+  using T = typename Ar::V;
   constexpr int NQ = AdvShape<NP>::NQ, NP3 = NP * NP * NP, NQ2 = NQ * NQ, NQ3 = NQ2 * NQ;
   constexpr int RS = AdvShape<NP>::RS, PS = AdvShape<NP>::PS;
-  // dynamic shared memory (advect_smem<T, NP>() bytes):
+  // dynamic shared memory (advect_smem<Ar, NP>() bytes):
   extern __shared__ __align__(16) unsigned char s_raw[];
   T* sI = reinterpret_cast<T*>(s_raw);   // [NQ * NP] interpolation, runtime-indexed rows and columns
   T* sD = sI + NQ * NP;                  // [NQ * NQ]
@@ -215,41 +263,49 @@ __global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
   T* s_ch = s_R + NQ * PS;               // [3 * NQ3] the contravariant wind
   const int e = blockIdx.x;
   const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
-  load_ops<T, NP, NQ>(Im, Dq, sI, sD);
+  load_ops<Ar, NP, NQ>(Im, Dq, sI, sD);
   const size_t eb = (size_t)e * NP3;
-  const T* G = Gq + (size_t)e * 9 * NQ3 + b * NQ + a;
+  const typename Ar::G* G = Gq + (size_t)e * 9 * NQ3 + b * NQ + a;
   // 1-2. contravariant wind at this thread's points, kept in shared memory
   const int pt0 = b * NQ + a;   // point (a, b, c) at pt0 + c * NQ2
 #pragma unroll
-  for (int c = 0; c < NQ; ++c) s_ch[pt0 + c * NQ2] = s_ch[NQ3 + pt0 + c * NQ2] = s_ch[2 * NQ3 + pt0 + c * NQ2] = T(0);
+  for (int c = 0; c < NQ; ++c)
+    s_ch[pt0 + c * NQ2] = s_ch[NQ3 + pt0 + c * NQ2] = s_ch[2 * NQ3 + pt0 + c * NQ2] = Ar::zero();
   for (int m = 0; m < 3; ++m) {
     __syncthreads();
-    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = cv[(size_t)m * nL + eb + q];
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = Ar::ld(cv, (size_t)m * nL + eb + q);
     __syncthreads();
     T cf[NQ];
-    to_gauss<T, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, cf);
+    to_gauss<Ar, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, cf);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
       const int pt = pt0 + c * NQ2;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) s_ch[d * NQ3 + pt] = fma(G[(d * 3 + m) * NQ3 + c * NQ2], cf[c], s_ch[d * NQ3 + pt]);
+      for (int d = 0; d < 3; ++d)
+        s_ch[d * NQ3 + pt] = Ar::mac(s_ch[d * NQ3 + pt], Ar::lg(G, (d * 3 + m) * NQ3 + c * NQ2), cf[c]);
     }
+  }
+  if constexpr (Ar::kNorm) {
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) s_ch[d * NQ3 + pt0 + c * NQ2] = Ar::norm(s_ch[d * NQ3 + pt0 + c * NQ2]);
   }
   // 3. every advected component
   for (int comp = 0; comp < ncomp; ++comp) {
     __syncthreads();
-    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = uv[(size_t)comp * nL + eb + q];
+    for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = Ar::ld(uv, (size_t)comp * nL + eb + q);
     __syncthreads();
     T uf[NQ];
-    to_gauss<T, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, uf);
+    to_gauss<Ar, NP, NQ>(s_src, s_t1, sI, P.Im, a, b, uf);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_U[c * PS + b * RS + a] = uf[c];
     T conv[NQ];
     {
       T ut[NQ];
-      eo_deriv<T, NP>(P, uf, ut);   // t-derivative along this thread's line
+      eo_deriv<Ar, NP>(P, uf, ut);   // t-derivative along this thread's line
 #pragma unroll
-      for (int c = 0; c < NQ; ++c) conv[c] = s_ch[2 * NQ3 + pt0 + c * NQ2] * ut[c];
+      for (int c = 0; c < NQ; ++c) conv[c] = Ar::mul(s_ch[2 * NQ3 + pt0 + c * NQ2], ut[c]);
     }
     __syncthreads();
     // r-derivative on the line (plane c = b, row j = a) -> s_R
@@ -258,13 +314,13 @@ __global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
       const int rb = a, rc = b;
 #pragma unroll
       for (int m = 0; m < NQ; ++m) v[m] = s_U[rc * PS + rb * RS + m];
-      eo_deriv<T, NP>(P, v, o);
+      eo_deriv<Ar, NP>(P, v, o);
 #pragma unroll
       for (int m = 0; m < NQ; ++m) s_R[rc * PS + rb * RS + m] = o[m];
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) conv[c] = fma(s_ch[pt0 + c * NQ2], s_R[c * PS + b * RS + a], conv[c]);
+    for (int c = 0; c < NQ; ++c) conv[c] = Ar::mac(conv[c], s_ch[pt0 + c * NQ2], s_R[c * PS + b * RS + a]);
     __syncthreads();
     // s-derivative on the column (plane c = b, column i = a) -> s_R
     {
@@ -272,20 +328,21 @@ __global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
       const int sa = a, sc = b;
 #pragma unroll
       for (int m = 0; m < NQ; ++m) v[m] = s_U[sc * PS + m * RS + sa];
-      eo_deriv<T, NP>(P, v, o);
+      eo_deriv<Ar, NP>(P, v, o);
 #pragma unroll
       for (int m = 0; m < NQ; ++m) s_R[sc * PS + m * RS + sa] = o[m];
     }
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < NQ; ++c) conv[c] = fma(s_ch[NQ3 + pt0 + c * NQ2], s_R[c * PS + b * RS + a], conv[c]);
+    for (int c = 0; c < NQ; ++c)
+      conv[c] = Ar::norm(Ar::mac(conv[c], s_ch[NQ3 + pt0 + c * NQ2], s_R[c * PS + b * RS + a]));
     // back to the GLL points: t-pass from registers into v2[k][b][a] (s_U reused)
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      T acc = T(0);
+      T acc = Ar::zero();
 #pragma unroll
-      for (int c = 0; c < NQ; ++c) acc = fma(P.Im[c * NP + k], conv[c], acc);
-      s_U[k * PS + b * RS + a] = acc;
+      for (int c = 0; c < NQ; ++c) acc = Ar::mac(acc, P.Im[c * NP + k], conv[c]);
+      s_U[k * PS + b * RS + a] = Ar::norm(acc);
     }
     __syncthreads();
     // s-pass: v1[k][j][a] = sum_b I[b][j] v2[k][b][a] (threads with b < NP own j = b)
@@ -295,25 +352,25 @@ __global__ void __launch_bounds__(AdvShape<NP>::T, (adv_min_blocks<T, NP>()))
       for (int q = 0; q < NQ; ++q) cb[q] = sI[q * NP + b];
 #pragma unroll 2
       for (int k = 0; k < NP; ++k) {
-        T acc = T(0);
+        T acc = Ar::zero();
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc = fma(cb[q], s_U[k * PS + q * RS + a], acc);
-        s_t1[(k * NP + b) * NQ + a] = acc;
+        for (int q = 0; q < NQ; ++q) acc = Ar::mac(acc, cb[q], s_U[k * PS + q * RS + a]);
+        s_t1[(k * NP + b) * NQ + a] = Ar::norm(acc);
       }
     }
     __syncthreads();
     // r-pass: w[k][j][i] = sum_a I[a][i] v1[k][j][a] (threads (i, j) = (a, b) with a, b < NP)
     if (a < NP && b < NP) {
-      T* out = wv + (size_t)comp * nL + eb;
+      typename Ar::S* out = wv + (size_t)comp * nL + eb;
       T ca[NQ];   // column a of I
 #pragma unroll
       for (int q = 0; q < NQ; ++q) ca[q] = sI[q * NP + a];
 #pragma unroll 2
       for (int k = 0; k < NP; ++k) {
-        T acc = T(0);
+        T acc = Ar::zero();
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc = fma(ca[q], s_t1[(k * NP + b) * NQ + q], acc);
-        out[(k * NP + b) * NP + a] = acc;
+        for (int q = 0; q < NQ; ++q) acc = Ar::mac(acc, ca[q], s_t1[(k * NP + b) * NQ + q]);
+        Ar::st(out, (size_t)(k * NP + b) * NP + a, acc);
       }
     }
   }
@@ -335,7 +392,7 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
   __shared__ double s_X[NQ3];
   const int e = blockIdx.x;
   const int a = threadIdx.x % NQ, b = threadIdx.x / NQ;
-  load_ops<double, NP, NQ>(Im, Dq, sI, sD);
+  load_ops<AdvPlain<double>, NP, NQ>(Im, Dq, sI, sD);
   const size_t eb = (size_t)e * NP3;
   double Jl[3][3][NQ];   // Jl[m][d][c] = dx_m / dr_d at Gauss point (a, b, c)
   const double* X[3] = {x, y, z};
@@ -345,7 +402,7 @@ __global__ void __launch_bounds__(AdvShape<NP>::T)
     for (int q = threadIdx.x; q < NP3; q += blockDim.x) s_src[q] = X[m][eb + q] - x0;
     __syncthreads();
     double line[NQ];
-    to_gauss<double, NP, NQ>(s_src, s_t1, sI, sI, a, b, line);
+    to_gauss<AdvPlain<double>, NP, NQ>(s_src, s_t1, sI, sI, a, b, line);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) s_X[(c * NQ + b) * NQ + a] = line[c];
     __syncthreads();
@@ -407,27 +464,28 @@ int cub_geom_launch(const Level& L, const double* Im, const double* Dq, const do
   return SEM_OK;
 }
 
-template <typename T, int NP>
-int advect_launch(const Level& L, const AdvData& A, const T* c, const T* u, T* w, int ncomp, const T* Gq,
-                  const T* Im, const T* Dq, cudaStream_t s) {
+template <class Ar, int NP>
+int advect_launch(const Level& L, const AdvData& A, const typename Ar::S* c, const typename Ar::S* u,
+                  typename Ar::S* w, int ncomp, const typename Ar::G* Gq, const typename Ar::G* Im,
+                  const typename Ar::G* Dq, cudaStream_t s) {
   constexpr int NQ = nq_of(NP), H = NQ / 2, N = NQ - 1;
-  AdvOps<T, NP> P{};
-  for (int q = 0; q < NQ * NP; ++q) P.Im[q] = (T)A.hIm[q];
+  AdvOps<typename Ar::V, NP> P{};
+  for (int q = 0; q < NQ * NP; ++q) P.Im[q] = Ar::host(A.hIm[q]);
   auto d = [&](int r, int q) { return A.hDq[r * NQ + q]; };
   for (int r = 0; r < H; ++r)
     for (int q = 0; q < H; ++q) {
-      P.ep[r * H + q] = (T)(0.5 * (d(r, q) + d(r, N - q)));
-      P.op[r * H + q] = (T)(0.5 * (d(r, q) - d(r, N - q)));
+      P.ep[r * H + q] = Ar::host(0.5 * (d(r, q) + d(r, N - q)));
+      P.op[r * H + q] = Ar::host(0.5 * (d(r, q) - d(r, N - q)));
     }
   if (NQ % 2 == 1)
     for (int r = 0; r < H; ++r) {
-      P.mc[r] = (T)d(r, H);
-      P.mr[r] = (T)d(H, r);
+      P.mc[r] = Ar::host(d(r, H));
+      P.mr[r] = Ar::host(d(H, r));
     }
-  constexpr size_t smem = advect_smem<T, NP>();
+  constexpr size_t smem = advect_smem<Ar, NP>();
   static PerDevice<bool> attr;
-  SEM_TRY(smem_attr_once(attr, (const void*)k_advect<T, NP>, smem));
-  k_advect<T, NP><<<L.E, AdvShape<NP>::T, smem, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w, P);
+  SEM_TRY(smem_attr_once(attr, (const void*)k_advect<Ar, NP>, smem));
+  k_advect<Ar, NP><<<L.E, AdvShape<NP>::T, smem, s>>>(L.E, ncomp, L.nL, c, u, Gq, Im, Dq, w, P);
   SEM_LAUNCH_CHECK();
   return SEM_OK;
 }
@@ -466,6 +524,14 @@ __global__ void k_minv(int64_t n, double* __restrict__ m, float* __restrict__ m3
 template <typename T>
 __global__ void k_wind(int64_t n, const T* __restrict__ c0, const T* __restrict__ c1, T th, T* __restrict__ c) {
   GRID_LOOP_ADV(l, n) c[l] = c0[l] + th * (c1[l] - c0[l]);
+}
+
+// (hi, lo) FP32 split of FP64 values
+__global__ void k_split_adv(int64_t n, const double* __restrict__ a, float2* __restrict__ b) {
+  GRID_LOOP_ADV(q, n) {
+    const ff v = ff_split(a[q]);
+    b[q] = make_float2(v.h, v.l);
+  }
 }
 
 // One RK4 stage on ncomp components: k = -minv z (z = QQ^T C w_stage);
@@ -561,40 +627,79 @@ int advect_build(Ctx& C, cudaStream_t s) {
   return SEM_OK;
 }
 
+// The FP32-pair copies of the cubature factors and the 1-D matrices (first pair evaluation).
+int advect_pairs_build(AdvData& A, const Level& L, cudaStream_t s) {
+  if (A.Gq2) return SEM_OK;
+  const int NQ = A.nq, NP = L.NP;
+  const size_t ng = (size_t)L.E * 9 * NQ * NQ * NQ;
+  float2 *g2 = nullptr, *i2 = nullptr, *d2 = nullptr;
+  if (cudaMalloc((void**)&g2, ng * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&i2, (size_t)NQ * NP * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc((void**)&d2, (size_t)NQ * NQ * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    if (g2) cudaFree(g2);
+    if (i2) cudaFree(i2);
+    set_detail("cudaMalloc of %zu bytes failed (FP32-pair cubature factors)", ng * sizeof(float2));
+    return SEM_ENOMEM;
+  }
+  k_split_adv<<<vgrid_adv((int64_t)ng), 256, 0, s>>>((int64_t)ng, A.Gq, g2);
+  k_split_adv<<<1, 256, 0, s>>>((int64_t)NQ * NP, A.Im, i2);
+  k_split_adv<<<1, 256, 0, s>>>((int64_t)NQ * NQ, A.Dq, d2);
+  SEM_LAUNCH_CHECK();
+  A.Gq2 = g2;
+  A.Im2 = i2;
+  A.Dq2 = d2;
+  return SEM_OK;
+}
+
 void advect_free(AdvData& A) {
-  void* ptrs[] = {A.Gq, A.Gq32, A.Im, A.Dq, A.wq, A.Im32, A.Dq32, A.minv, A.minv32, A.ws};
+  void* ptrs[] = {A.Gq, A.Gq32, A.Gq2, A.Im, A.Dq, A.wq, A.Im32, A.Dq32, A.Im2, A.Dq2, A.minv, A.minv32, A.ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   A = AdvData();
 }
 
-int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s) {
+int advect_apply(Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s) {
   const Level& L = C.lev[0];
-  const AdvData& A = C.adv;
-  if (prec == SEM_FP64) {
+  AdvData& A = C.adv;
+  if (prec == SEM_FP64P) {
+    SEM_TRY(advect_pairs_build(A, L, s));
     const double *cc = (const double*)c, *uu = (const double*)u;
     double* ww = (double*)w;
     switch (L.NP) {
-      ADV_DISPATCH(3, (advect_launch<double, 3>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(4, (advect_launch<double, 4>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(5, (advect_launch<double, 5>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(6, (advect_launch<double, 6>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(7, (advect_launch<double, 7>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(8, (advect_launch<double, 8>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
-      ADV_DISPATCH(9, (advect_launch<double, 9>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(3, (advect_launch<AdvPair, 3>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(4, (advect_launch<AdvPair, 4>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(5, (advect_launch<AdvPair, 5>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(6, (advect_launch<AdvPair, 6>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(7, (advect_launch<AdvPair, 7>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(8, (advect_launch<AdvPair, 8>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      ADV_DISPATCH(9, (advect_launch<AdvPair, 9>(L, A, cc, uu, ww, ncomp, A.Gq2, A.Im2, A.Dq2, s)))
+      default: break;
+    }
+  } else if (prec == SEM_FP64) {
+    const double *cc = (const double*)c, *uu = (const double*)u;
+    double* ww = (double*)w;
+    switch (L.NP) {
+      ADV_DISPATCH(3, (advect_launch<AdvPlain<double>, 3>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(4, (advect_launch<AdvPlain<double>, 4>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(5, (advect_launch<AdvPlain<double>, 5>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(6, (advect_launch<AdvPlain<double>, 6>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(7, (advect_launch<AdvPlain<double>, 7>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(8, (advect_launch<AdvPlain<double>, 8>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
+      ADV_DISPATCH(9, (advect_launch<AdvPlain<double>, 9>(L, A, cc, uu, ww, ncomp, A.Gq, A.Im, A.Dq, s)))
       default: break;
     }
   } else {
     const float *cc = (const float*)c, *uu = (const float*)u;
     float* ww = (float*)w;
     switch (L.NP) {
-      ADV_DISPATCH(3, (advect_launch<float, 3>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(4, (advect_launch<float, 4>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(5, (advect_launch<float, 5>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(6, (advect_launch<float, 6>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(7, (advect_launch<float, 7>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(8, (advect_launch<float, 8>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
-      ADV_DISPATCH(9, (advect_launch<float, 9>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(3, (advect_launch<AdvPlain<float>, 3>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(4, (advect_launch<AdvPlain<float>, 4>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(5, (advect_launch<AdvPlain<float>, 5>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(6, (advect_launch<AdvPlain<float>, 6>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(7, (advect_launch<AdvPlain<float>, 7>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(8, (advect_launch<AdvPlain<float>, 8>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
+      ADV_DISPATCH(9, (advect_launch<AdvPlain<float>, 9>(L, A, cc, uu, ww, ncomp, A.Gq32, A.Im32, A.Dq32, s)))
       default: break;
     }
   }
@@ -610,7 +715,8 @@ int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int 
   const Level& L = C.lev[0];
   AdvData& A = C.adv;
   const int64_t nL = L.nL, n = (int64_t)ncomp * nL;
-  const size_t esz = prec == SEM_FP64 ? 8 : 4;
+  const int vp = prec == SEM_FP32 ? SEM_FP32 : SEM_FP64;   // the vectors' type (FP64 with the pair operator)
+  const size_t esz = vp == SEM_FP64 ? 8 : 4;
   if (!A.minv) {
     if (cudaMalloc(&A.minv, nL * 8) != cudaSuccess || cudaMalloc(&A.minv32, nL * 4) != cudaSuccess) {
       cudaGetLastError();
@@ -644,7 +750,7 @@ int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int 
   auto wind = [&](double t) -> const void* {
     if (!c1) return c0;
     const double th = (t - t0) / (t1 - t0);
-    if (prec == SEM_FP64)
+    if (vp == SEM_FP64)
       k_wind<double><<<vgrid_adv(3 * nL), 256, 0, s>>>(3 * nL, (const double*)c0, (const double*)c1, th, (double*)cb);
     else
       k_wind<float><<<vgrid_adv(3 * nL), 256, 0, s>>>(3 * nL, (const float*)c0, (const float*)c1, (float)th,
@@ -655,11 +761,11 @@ int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int 
     const void* c = wind(t);
     SEM_LAUNCH_CHECK();
     SEM_TRY(advect_apply(C, prec, c, win, zb, ncomp, s));
-    for (int q = 0; q < ncomp; ++q) SEM_TRY(gs_apply(L, prec, static_cast<char*>(zb) + q * nL * esz, false, s));
+    for (int q = 0; q < ncomp; ++q) SEM_TRY(gs_apply(L, vp, static_cast<char*>(zb) + q * nL * esz, false, s));
     return SEM_OK;
   };
   auto stage = [&](double cw, int mode) -> int {
-    if (prec == SEM_FP64)
+    if (vp == SEM_FP64)
       k_rk_stage<double><<<vgrid_adv(n), 256, 0, s>>>(n, nL, (const double*)zb, A.minv, (double*)w, (double*)wsb,
                                                       (double*)accb, cw, mode);
     else

@@ -165,8 +165,10 @@ struct AdvData {
   int nq = 0;
   double* Gq = nullptr;      // [E][9][nq^3] w J dr_d/dx_m at the Gauss points
   float* Gq32 = nullptr;
+  float2* Gq2 = nullptr;      // FP32-pair split of Gq (built on the first pair evaluation)
   double *Im = nullptr, *Dq = nullptr, *wq = nullptr;   // GLL -> Gauss interpolation, Gauss derivative, weights
   float *Im32 = nullptr, *Dq32 = nullptr;
+  float2 *Im2 = nullptr, *Dq2 = nullptr;
   double hIm[14 * 9] = {0};   // host copies (nq <= 14, N + 1 <= 9)
   double hDq[14 * 14] = {0};
   // characteristics substeps: inverse assembled mass and RK workspace (allocated on first use)
@@ -302,7 +304,7 @@ int arnoldi_lmax_asm(Ctx& C, int l, double h1, double h2, const double* v0, int 
 // ---- advect.cu: dealiased advection operator
 int advect_build(Ctx& C, cudaStream_t s);
 void advect_free(AdvData& A);
-int advect_apply(const Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s);
+int advect_apply(Ctx& C, int prec, const void* c, const void* u, void* w, int ncomp, cudaStream_t s);
 int char_advance(Ctx& C, int prec, const void* c0, const void* c1, void* w, int ncomp, double t0, double t1,
                  int nsub, cudaStream_t s);
 

@@ -616,9 +616,9 @@ int sem_asm_apply(sem_ctx* h, int level, int prec, const void* r, void* z, doubl
 int sem_advect(sem_ctx* h, int prec, const void* c, const void* u, void* w, int ncomp, int flags, void* stream) {
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));
-  if (!c || !u || !w || w == u || w == c || ncomp < 1 || (prec != SEM_FP64 && prec != SEM_FP32) ||
+  if (!c || !u || !w || w == u || w == c || ncomp < 1 || (prec != SEM_FP64 && prec != SEM_FP32 && prec != SEM_FP64P) ||
       (flags & ~SEM_ADV_ASSEMBLE)) {
-    set_detail("sem_advect: NULL or aliased vector, ncomp < 1, precision other than FP64/FP32, or unknown flag");
+    set_detail("sem_advect: NULL or aliased vector, ncomp < 1, precision other than FP64/FP32/FP64P, or unknown flag");
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -626,9 +626,10 @@ int sem_advect(sem_ctx* h, int prec, const void* c, const void* u, void* w, int 
   SEM_TRY(advect_apply(*C, prec, c, u, w, ncomp, s));
   if (flags & SEM_ADV_ASSEMBLE) {
     const Level& L = C->lev[0];
-    const size_t esz = prec == SEM_FP64 ? 8 : 4;
+    const int vp = prec == SEM_FP32 ? SEM_FP32 : SEM_FP64;
+    const size_t esz = vp == SEM_FP64 ? 8 : 4;
     for (int q = 0; q < ncomp; ++q)
-      SEM_TRY(gs_apply(L, prec, static_cast<char*>(w) + (size_t)q * L.nL * esz, false, s));
+      SEM_TRY(gs_apply(L, vp, static_cast<char*>(w) + (size_t)q * L.nL * esz, false, s));
   }
   return SEM_OK;
 }
@@ -638,8 +639,8 @@ int sem_char_advance(sem_ctx* h, int prec, const void* c0, const void* c1, void*
   Ctx* C = ctx_of(h);
   SEM_TRY(check_level(C, 0));
   if (!c0 || !w || w == c0 || (c1 && w == c1) || ncomp < 1 || nsub < 1 || !(t1 != t0) ||
-      (prec != SEM_FP64 && prec != SEM_FP32)) {
-    set_detail("sem_char_advance: NULL or aliased vector, ncomp or nsub < 1, t1 == t0, or precision other than FP64/FP32");
+      (prec != SEM_FP64 && prec != SEM_FP32 && prec != SEM_FP64P)) {
+    set_detail("sem_char_advance: NULL or aliased vector, ncomp or nsub < 1, t1 == t0, or precision other than FP64/FP32/FP64P");
     return SEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
