@@ -38,6 +38,8 @@ struct ArF64 {
   __device__ static V zero() { return 0.0; }
   __device__ static V add(V a, V b) { return a + b; }
   __device__ static V sub(V a, V b) { return a - b; }
+  __device__ static V add_u(V a, V b) { return a + b; }
+  __device__ static V sub_u(V a, V b) { return a - b; }
   __device__ static V mul(V a, V b) { return a * b; }
   __device__ static V mac(V acc, V a, V b) { return fma(a, b, acc); }
   __device__ static V tidy(V a) { return a; }
@@ -59,6 +61,10 @@ struct ArPair {
   __device__ static V zero() { return {0.f, 0.f}; }
   __device__ static V add(V a, V b) { return ff_add(a, b); }
   __device__ static V sub(V a, V b) { return ff_sub(a, b); }
+  // the additions inside the even-odd line transforms, whose results only enter further
+  // error-free additions and products, skip the renormalisation
+  __device__ static V add_u(V a, V b) { return ff_add_u(a, b); }
+  __device__ static V sub_u(V a, V b) { return ff_sub_u(a, b); }
   __device__ static V mul(V a, V b) { return ff_mul(a, b); }
   __device__ static V mac(V acc, V a, V b) { return ff_mac(acc, a, b); }
   __device__ static V tidy(V a) { return ff_norm(a); }
@@ -111,8 +117,8 @@ __device__ __forceinline__ void eo_apply(const EOMat<Ar>& M, const typename Ar::
   V s[H], d[H];
 #pragma unroll
   for (int b = 0; b < H; ++b) {
-    s[b] = Ar::add(v[b], v[N - b]);
-    d[b] = Ar::sub(v[b], v[N - b]);
+    s[b] = Ar::add_u(v[b], v[N - b]);
+    d[b] = Ar::sub_u(v[b], v[N - b]);
   }
 #pragma unroll
   for (int a = 0; a < H; ++a) {
@@ -124,8 +130,8 @@ __device__ __forceinline__ void eo_apply(const EOMat<Ar>& M, const typename Ar::
       od = Ar::mac(od, M.op[a * H + b], d[b]);
     }
     if (NP % 2 == 1) ev = Ar::mac(ev, M.mc[a], v[H]);
-    o[a] = Ar::add(ev, od);
-    o[N - a] = Ar::sub(od, ev);
+    o[a] = Ar::add_u(ev, od);
+    o[N - a] = Ar::sub_u(od, ev);
   }
   if (NP % 2 == 1) {
     V m = Ar::mul(M.mr[0], d[0]);
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(NP* NP* eo_epb<NP>(), (eo_min_blocks<Ar, NP>()
     const typename Ar::GT* Be = G + (size_t)e * 7 * NP3 + 6 * NP3 + ij;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-      const V st = Ar::add(Ar::add(A[k * PS + j * RS + i], B[k * PS + j * RS + i]), ot[k]);
+      const V st = Ar::add_u(Ar::add_u(A[k * PS + j * RS + i], B[k * PS + j * RS + i]), ot[k]);
       const V hb = Ar::mul(Ar::mul(h2, Ar::gl(Be, k * NP2)), ru[k]);
       Ar::out(w, ebase + k * NP2 + ij, VARH1 ? Ar::add(st, hb) : Ar::mac(hb, h1, st));
     }

@@ -46,6 +46,20 @@ __device__ __forceinline__ ff ff_add(const ff a, const ff b) {
 
 __device__ __forceinline__ ff ff_sub(const ff a, const ff b) { return ff_add(a, ff{-b.h, -b.l}); }
 
+// a + b without the final renormalisation: hi is fl(a.h + b.h) and lo gathers its exact
+// rounding error and a.l + b.l. The pair's value is the same to the same order (about
+// 2^-48 of |a| + |b|); lo may exceed ulp(hi)/2 after cancellation, which the error-free
+// transforms of ff_add and ff_mac accept as inputs (TwoSum and the TwoProduct of the
+// high parts stay exact; the low cross terms are rounded relative to |lo|).
+__device__ __forceinline__ ff ff_add_u(const ff a, const ff b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float t = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, t)), __fsub_rn(b.h, t));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_sub_u(const ff a, const ff b) { return ff_add_u(a, ff{-b.h, -b.l}); }
+
 // x * y, unnormalised
 __device__ __forceinline__ ff ff_mul(const ff x, const ff y) {
   const float p = __fmul_rn(x.h, y.h);
