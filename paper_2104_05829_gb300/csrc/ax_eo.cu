@@ -92,13 +92,14 @@ struct Pad3 {
 
 // Blocks per SM requested from the register allocator: at N = 7 four 192-thread blocks (at
 // most 85 registers; five made the pair kernel spill and run slower). The pair kernel at other
-// orders: three blocks (two for N = 8..10), which took N = 3, 5 and 11 from 0.390, 0.416 and
-// 1.347 ms to 0.334, 0.371 and 0.749 ms at 16.8M points (the register allocator otherwise
-// leaves one block of up to 252 registers per SM); the FP64 kernel is bound by its pipe at
-// any occupancy.
+// orders: three blocks, four at N = 9 (one 100-thread element per block there), against the
+// register allocator's default of one or two blocks of up to 255 registers: at 16.8M points
+// N = 3, 5, 11 took 0.390, 0.416, 1.347 ms with one block and 0.334, 0.371, 0.749 ms with three,
+// and N = 8, 9, 10 took 0.518, 0.848, 0.625 ms with two blocks and 0.453, 0.634 (four),
+// 0.492 ms; the FP64 kernel is bound by its pipe at any occupancy.
 template <class Ar, int NP>
 __host__ __device__ constexpr int eo_min_blocks() {
-  return NP == 8 ? 4 : (Ar::kPairs ? ((NP >= 9 && NP <= 11) ? 2 : 3) : 1);
+  return NP == 8 ? 4 : (Ar::kPairs ? (NP == 10 ? 4 : 3) : 1);
 }
 
 template <int NP>
